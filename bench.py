@@ -1,0 +1,320 @@
+"""Benchmark: batched parametric slab solves to a 1e-6 relative flux change.
+
+Workload: 4096 independent single-group slabs (10 cm), cells ~ U{64..2048},
+Gauss-Legendre S_N with N even ~ U{8..64}, sinusoidal or piecewise
+coefficients and clipped Fourier sources from per-instance seeds (the
+batched parametric workload).  One step solves the whole batch: the warm
+start when a trained operator is available, then the FP32 source iterations
+with FP64 norms, all through the C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank solves its own batch
+(rank-seeded): weak scaling, no collective on the data path.
+"""
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "solves/s to 1e-6 residual (batched slab S_N solve)"
+UNIT = "solves/s"
+TOL = 1e-6
+WORKLOAD = ("4096 slabs, cells U{64..2048}, GL S_N N even U{8..64}, sinusoidal or "
+            "piecewise coefficients, Fourier sources, vacuum, tol 1e-6 rel. L2 flux change")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# --------------------------------------------------------------- oracle leg
+def _oracle_one(args):
+    I, N, L, sigt, sigs, Q = args
+    from oracle import quadrature as Qd
+    from oracle import transport as T
+    P = T.uniform_slab(I, L, sigt, sigs, Q=Q)
+    T.source_iteration(P, Qd.gauss_legendre(N), tol=TOL, itmax=200000)
+    return I * N
+
+
+def oracle_rate(insts, seconds, seed=0, pool=None):
+    """Solve a random sample of the batch with the FP64 oracle on all host
+    cores for about `seconds`; returns (solves/s, cores, n_solved, elapsed)."""
+    cores = os.cpu_count() or 1
+    own = pool is None
+    if own:
+        pool = mp.get_context("spawn").Pool(cores)
+    order = np.random.default_rng(seed).permutation(len(insts))
+    jobs = [(insts[b].I, insts[b].N, insts[b].L, insts[b].sigt, insts[b].sigs, insts[b].Q)
+            for b in order]
+    t0 = time.perf_counter()
+    done = 0
+    it = pool.imap_unordered(_oracle_one, jobs, chunksize=1)
+    while True:
+        try:
+            it.next(timeout=max(0.01, seconds - (time.perf_counter() - t0)))
+            done += 1
+        except (mp.TimeoutError, StopIteration):
+            break
+        if time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    if own:
+        pool.terminate()
+        pool.join()
+    return done / el if el > 0 else 0.0, cores, done, el
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    def __init__(self, idx, path):
+        self.idx, self.path, self.p = idx, path, None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if len(r) > 8]
+        mx = [float(r[2]) for r in rows if len(r) > 8]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, v in zip(names, r[5:9]):
+                if v.strip().lower() in ("active", "0x1", "1"):
+                    reasons.add(k)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    insts = W.config5(seed=5 + rank)
+    cores = os.cpu_count() or 1
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        run_reference(args, insts, world)
+        return
+
+    # the oracle's process pool starts before the first GPU call
+    pool = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pool = mp.get_context("spawn").Pool(cores)
+
+    import torch
+    import torch.distributed as dist
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_2509_01416_gb300 import Solver, capi
+    from tests.helpers import slab_batch_arrays
+
+    n, wdt, order, sigt, sigs, src, _ = slab_batch_arrays(insts)
+    B, Ctot = len(insts), int(n.sum())
+    stream = torch.cuda.Stream()
+    s = Solver(local)
+    s.set_stream(stream.cuda_stream)
+    s.set_slabs(n, wdt, order, sigt, sigs, source=src)
+    phi_dev = torch.empty(Ctot, dtype=torch.float64, device="cuda")
+
+    def step():
+        return s.solve_fixed_source_dev(phi_dev.data_ptr(), tol=TOL, itmax=200000,
+                                        precision=0)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(max(3, args.warmup)):
+        info = step()
+    torch.cuda.synchronize()
+    plain_iters = info["iterations"].astype(np.float64)
+
+    # ---- timed region (device-resident inputs)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+    clk = Clocks(local, os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % rank))
+    s.set_timing(True)
+    barrier()
+    torch.cuda.synchronize()
+    with clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            info = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    tm = s.timing()
+    s.set_timing(False)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * B * args.steps / (ms_max / 1e3)
+
+    # ---- end to end through the C ABI with host buffers
+    h2d = sum(a.nbytes for a in (n, wdt, order, sigt, sigs, src))
+    d2h = 8 * Ctot + 8 * B
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.set_slabs(n, wdt, order, sigt, sigs, source=src)
+        phi_h, _info = s.solve_fixed_source(tol=TOL, itmax=200000, precision=0)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * B * args.steps / float(te.item())
+
+    if rank != 0:
+        s.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    peaks, src_peak = _peaks()
+    ck = clk.summary() or {}
+    smx = float(peaks.get("sm_max_mhz", 2070.0))
+    # special-function-unit reciprocal rate: 16 per SM per clock, 152 SMs
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    mufu_peak = n_sm * 16 * smx * 1e6
+    sweep_s = tm["sweep_ms"] / 1e3
+    upd = tm["cell_angle_updates"]
+    achieved = upd / sweep_s if sweep_s > 0 else 0.0
+    cells_iter = float(np.sum(info["iterations"].astype(np.float64) * n))
+    alg_bytes = 20.0 * cells_iter * args.steps        # 20 B per cell per iteration
+    sweep_gbs = alg_bytes / sweep_s / 1e9 if sweep_s > 0 else 0.0
+
+    cpu = None
+    if pool is not None:
+        rate, cores_used, nsol, el = oracle_rate(insts, args.cpu_seconds, pool=pool)
+        pool.terminate()
+        pool.join()
+        cpu = {"value": rate, "unit": UNIT, "cores": cores_used, "kind": "oracle",
+               "sample": "%d instances of a random permutation of the batch solved by the "
+                         "FP64 oracle (zero guess, tol 1e-6) in %.1f s on %d processes"
+                         % (nsol, el, cores_used)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "precision": {"sweep": "f32", "norms": "f64"},
+        "data": "synthetic (seeded; paper's samples unpublished)",
+        "config": {"workload": WORKLOAD, "instances_per_gpu": B, "cells_per_gpu": Ctot,
+                   "l2": "inputs larger than L2: %.0f MB resident per GPU" %
+                         ((Ctot * (3 * 8 + 24)) / 1e6),
+                   "warm_start": "none (plain zero guess)"},
+        "iterations": {"plain_mean": float(np.mean(plain_iters)),
+                       "plain_max": int(np.max(plain_iters))},
+        "clocks": ck,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(tm["launches"]),
+        "roofline": {"bound": "alu", "kernel": "sn1d_kernel<float>", "achieved": achieved,
+                     "peak": mufu_peak, "unit": "cell-angle updates/s",
+                     "frac": achieved / mufu_peak if mufu_peak else None, "traffic": None,
+                     "peak_source": "SFU reciprocal rate 16/clk/SM x %d SMs x %.0f MHz "
+                                    "(sm_max_mhz, %s)" % (n_sm, smx, src_peak),
+                     "sweep_ms_per_step": tm["sweep_ms"] / args.steps,
+                     "sweep_algorithmic_gbs": sweep_gbs,
+                     "sweep_algorithmic_frac_of_hbm": sweep_gbs / float(peaks.get("hbm_gbs", 6800.0))},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line))
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args, insts, world):
+    """The oracle as it stands, on the host cores: each step a bounded sample."""
+    cores = os.cpu_count() or 1
+    pool = mp.get_context("spawn").Pool(cores)
+    per = max(1.0, args.cpu_seconds / 3.0)
+    for _ in range(args.warmup):
+        oracle_rate(insts, min(per, 2.0), seed=1, pool=pool)
+    tot_s, tot_n = 0.0, 0
+    for k in range(args.steps):
+        rate, _, nsol, el = oracle_rate(insts, per, seed=100 + k, pool=pool)
+        tot_s += el
+        tot_n += nsol
+    pool.terminate()
+    pool.join()
+    value = tot_n / tot_s if tot_s > 0 else 0.0
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot_s / max(1, args.steps), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)",
+            "config": {"workload": WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "per step: instances of a random permutation solved "
+                                       "in %.1f s by the FP64 oracle (zero guess)" % per},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

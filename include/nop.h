@@ -1,0 +1,230 @@
+/*
+ * nop.h -- C ABI of the GB300 discrete-ordinates transport solver with
+ * equation-recast neural-operator warm start (MD-PNOP, arXiv 2509.01416).
+ *
+ * The library solves the steady neutron transport equation by the S_N method
+ * (diamond-difference sweeps inside source iteration, Sec. 5.1 Eq. 12 and the
+ * iteration operator M of Sec. 3.1 Eq. 3a/4b), the k-eigenvalue problem by
+ * power iteration with inner sweeps (Sec. 5.2 Eq. 26, App. A2 Eq. A2-A4),
+ * multigroup problems (Sec. 5.3 Eq. 27-29), and warm-starts either solve with
+ * a neural operator trained at one parameter point p* whose parameter mismatch
+ * is recast as an extra source (Sec. 3.1 Eq. 7, Sec. 3.2 Eq. 8-10b, Sec. 5.1
+ * Eq. 24, App. A2 Eq. A5-A6).
+ *
+ * Conventions for every entry point:
+ *   - Return value: NOP_OK (0) on success, a negative NOP_E* code otherwise.
+ *     nop_status_str() names a code; nop_last_error() returns a message for
+ *     the last failing call on that context.
+ *   - Pointers are host pointers unless an entry point or a flag says
+ *     "device".  The caller owns every buffer it passes; the library copies
+ *     inputs in and writes outputs into caller buffers before returning
+ *     (device outputs: enqueued on the context stream, see NOP_OUT_DEVICE).
+ *   - All floating-point host arrays are IEEE double; device-side arithmetic
+ *     precision is chosen per call (nop_solve_opts.precision).
+ *   - A context is used by one host thread at a time.  All GPU work of a
+ *     context runs on its stream (nop_set_stream).
+ *   - Array layouts are "group-major": for a field f with G groups over C
+ *     cells the value of group g in cell c sits at f[g * C + c].  Slab cells
+ *     are numbered instance by instance (all cells of instance 0, then of
+ *     instance 1, ...); x-y cells are row-major, c = j * nx + i.
+ */
+#ifndef NOP_H
+#define NOP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define NOP_OK         0
+#define NOP_EINVAL    -1   /* an argument is out of range or inconsistent      */
+#define NOP_ECUDA     -2   /* a CUDA runtime call failed                        */
+#define NOP_ENOMEM    -3   /* device or host allocation failed                  */
+#define NOP_ENOCONV   -4   /* iteration cap reached; outputs hold the last iterate */
+#define NOP_EDIVERGE  -5   /* recast iteration diverged; a plain guess was used */
+#define NOP_ETIMEOUT  -6   /* a device-side wait hit its limit                  */
+#define NOP_ENAN      -7   /* a non-finite value appeared in a norm             */
+#define NOP_ESTATE    -8   /* call out of order (e.g. solve before set_problem) */
+
+/* ------------------------------------------------------------ enumerations */
+#define NOP_GEOM_SLAB  1   /* batch of independent 1D slabs                  */
+#define NOP_GEOM_XY    2   /* one 2D x-y rectangle                           */
+
+#define NOP_BC_VACUUM      0
+#define NOP_BC_REFLECTIVE  1
+
+#define NOP_PREC_F32   0   /* FP32 sweeps; FP64 norms, k ratio and tests     */
+#define NOP_PREC_F64   1   /* FP64 throughout                                */
+
+#define NOP_WARM_NONE    0 /* plain guess: zero flux (fixed source), flat flux and k=1 (eigen) */
+#define NOP_WARM_RECAST  1 /* neural-operator recast warm start (needs a network) */
+
+/* flags of nop_solve_opts.flags */
+#define NOP_PHI0_DEVICE  1 /* phi0 is a device pointer                        */
+#define NOP_OUT_DEVICE   2 /* phi_out / k_out are device pointers; the call does
+                              not synchronise (results valid once the context
+                              stream reaches this point)                      */
+
+typedef struct nop_ctx nop_ctx;
+
+/* Problem description, copied into device memory by nop_set_problem.
+ *
+ * geometry == NOP_GEOM_SLAB: n_inst independent slabs.  Instance b has
+ *   n_cells[b] equal cells over [0, width[b]] and Gauss-Legendre order
+ *   order[b] (even, 2..128).  C = sum_b n_cells[b].
+ * geometry == NOP_GEOM_XY: one nx-by-ny rectangle of lx-by-ly with the
+ *   level-symmetric S8 set (40 directions in the x-y plane); n_inst must be 1,
+ *   order[0] must be 8.  C = nx * ny.
+ *
+ * Coefficients (Eq. 12, 26, 27-29), all group-major over C cells:
+ *   sigma_t   [G*C]      total cross section (> 0)
+ *   sigma_s   [G*G*C]    scattering from g' into g at [(g'*G + g)*C + c]
+ *   source    [G*C]      isotropic external source S (NULL for eigenproblems)
+ *   nu_sigma_f[G*C]      production nu*Sigma_f (NULL for fixed source)
+ *   chi       [G]        fission spectrum (NULL for fixed source)
+ * Boundary conditions: bc[0..1] = slab left/right (applied to every
+ *   instance); bc[0..3] = x=0, x=lx, y=0, y=ly for x-y.
+ */
+typedef struct {
+    int geometry;
+    int n_inst;
+    const int *n_cells;      /* slab: [n_inst] */
+    const double *width;     /* slab: [n_inst] */
+    const int *order;        /* [n_inst] quadrature order                   */
+    int nx, ny;              /* x-y only */
+    double lx, ly;           /* x-y only */
+    int n_groups;
+    const double *sigma_t;
+    const double *sigma_s;
+    const double *source;
+    const double *nu_sigma_f;
+    const double *chi;
+    int bc[4];
+} nop_problem;
+
+/* Solver options.  Convergence is the relative L2 change of the scalar flux
+ * between successive iterates, ||phi_new - phi_old|| / ||phi_new|| over all
+ * cells and groups of an instance, computed in FP64 on the device. */
+typedef struct {
+    double tol;            /* fixed source: flux tolerance; eigen: outer flux tolerance */
+    double tol_k;          /* eigen: |k_new - k_old| / k_new                   */
+    double tol_inner;      /* eigen: inner source-iteration tolerance          */
+    int itmax;             /* fixed source: max iterations; eigen: max outers  */
+    int itmax_inner;       /* eigen: max inner iterations per outer            */
+    int precision;         /* NOP_PREC_F32 or NOP_PREC_F64                     */
+    int warm_start;        /* NOP_WARM_NONE or NOP_WARM_RECAST                 */
+    double recast_tol;     /* recast loop tolerance (Eq. 24)                   */
+    int recast_itmax;      /* recast loop iteration cap                        */
+    int flags;             /* NOP_PHI0_DEVICE | NOP_OUT_DEVICE                 */
+} nop_solve_opts;
+
+/* Per-call statistics (host struct).  Per-instance arrays are optional
+ * caller buffers of n_inst entries (host memory), or NULL. */
+typedef struct {
+    int status;              /* worst status over instances (0 or NOP_E*)    */
+    int max_iterations;      /* max over instances of source iterations (fixed
+                                source) or total inner iterations (eigen)    */
+    long long sum_iterations;/* sum over instances                           */
+    int max_outer;           /* eigen: outer iterations                      */
+    int recast_iterations;   /* NO recast iterations of the warm start (max)  */
+    int recast_status;       /* worst recast status                          */
+    double max_change;       /* final relative change, max over instances    */
+    int *inst_iterations;    /* optional [n_inst] out                        */
+    int *inst_status;        /* optional [n_inst] out                        */
+} nop_stats;
+
+/* ------------------------------------------------------------ lifecycle */
+
+/* Create a context on CUDA device `device`.  *out receives the handle.
+ * Errors: NOP_EINVAL (out NULL), NOP_ECUDA (device unusable). */
+int nop_create(nop_ctx **out, int device);
+
+/* Free every device buffer of the context and the context itself.  NULL is
+ * accepted and ignored. */
+int nop_destroy(nop_ctx *ctx);
+
+/* Use `stream` (a cudaStream_t, or NULL for the context's own stream) for all
+ * later GPU work of the context.  The caller keeps the stream alive. */
+int nop_set_stream(nop_ctx *ctx, void *stream);
+
+/* Name of a status code (static string). */
+const char *nop_status_str(int status);
+
+/* Message describing the last failure on ctx (static per context). */
+const char *nop_last_error(nop_ctx *ctx);
+
+/* --------------------------------------------------------------- problem */
+
+/* Copy a problem into device memory, replacing the previous one
+ * (Sec. 5.1 Eq. 12, Sec. 5.2 Eq. 26, Sec. 5.3 Eq. 27-29 define its terms).
+ * Also builds the angular quadratures on the device: Gauss-Legendre (1D) and
+ * level-symmetric S8 (x-y).
+ * Errors: NOP_EINVAL for bad sizes/orders/NULL arrays, NOP_ENOMEM, NOP_ECUDA. */
+int nop_set_problem(nop_ctx *ctx, const nop_problem *p);
+
+/* Read back the quadrature built for instance `inst` (slab: N nodes ascending
+ * with weights summing to 2; x-y: 40 directions mu, eta with weights summing
+ * to 1, order of quadrants (-,-), (+,-), (-,+), (+,+)).  `eta` may be NULL for
+ * slabs.  n_out receives the node count; arrays must hold 128 (slab) / 40 (x-y)
+ * entries. */
+int nop_get_quadrature(nop_ctx *ctx, int inst, double *mu, double *eta,
+                       double *w, int *n_out);
+
+/* -------------------------------------------------------------- solvers */
+
+/* Fixed-source solve by source iteration (Sec. 3.1 Eq. 3a/4b, Sec. 5.1
+ * Eq. 20; multigroup: Gauss-Seidel over groups, Sec. 5.3).
+ * phi0:    initial flux [G*C], or NULL for the zero guess (ignored when
+ *          opts->warm_start == NOP_WARM_RECAST: the recast prediction, Eq. 9a,
+ *          is used instead).
+ * phi_out: converged scalar flux [G*C].
+ * stats:   may be NULL.
+ * Errors: NOP_ESTATE (no problem / source missing / warm start without a
+ * network), NOP_ENOCONV (some instance hit itmax; phi_out holds the last
+ * iterate), NOP_ENAN, NOP_ECUDA. */
+int nop_solve_fixed_source(nop_ctx *ctx, const nop_solve_opts *opts,
+                           const double *phi0, double *phi_out, nop_stats *stats);
+
+/* k-eigenvalue solve by power iteration with inner source iteration
+ * (Sec. 5.2 Eq. 26, App. A2 Eq. A2-A4).  The flux is normalised to unit
+ * production, sum nu*Sigma_f * phi * cell volume = 1, and
+ * k_{n+1} = k_n * production(phi_{n+1/2}).
+ * phi0 / k0: initial guess (phi0 NULL: flat flux; k0 <= 0: 1.0); with
+ *            NOP_WARM_RECAST the simple-preconditioning prediction (App. A2
+ *            Eq. A5) replaces both (Eq. A6).
+ * k_out:     [n_inst] eigenvalues.
+ * Errors: as nop_solve_fixed_source. */
+int nop_solve_eigen(nop_ctx *ctx, const nop_solve_opts *opts, const double *phi0,
+                    double k0, double *phi_out, double *k_out, nop_stats *stats);
+
+/* --------------------------------------------------------------- tracing */
+
+/* Device-side phase times accumulated since timing was enabled. */
+typedef struct {
+    double sweep_ms;         /* solver kernels (sweeps, norms, eigen updates)    */
+    double operator_ms;      /* neural-operator kernels (inference, recast loop)  */
+    double setup_ms;         /* data preparation / result conversion kernels      */
+    long long launches;      /* kernels this library launched                    */
+    long long sweep_launches;/* of which solver kernels                          */
+    double cell_angle_updates; /* algorithmic sweep work: sum over solved
+                                  instances of iterations x cells x angles x
+                                  groups (one diamond-difference cell update per
+                                  cell, direction and group)                     */
+} nop_timings;
+
+/* enable != 0: from now on record CUDA events around every kernel phase on
+ * the context stream and count launches (totals reset); 0: stop recording.
+ * Recording adds no synchronisation. */
+int nop_set_timing(nop_ctx *ctx, int enable);
+
+/* Synchronise the context stream and return the totals since the last
+ * nop_set_timing(ctx, 1). */
+int nop_get_timing(nop_ctx *ctx, nop_timings *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NOP_H */

@@ -1,0 +1,164 @@
+"""GB300-native S_N transport solver with equation-recast neural-operator warm start.
+
+The compute lives in libnop.so (hand-written sm_103a CUDA behind the C ABI of
+include/nop.h).  ``capi`` is the ctypes binding under the C names; ``Solver``
+below marshals numpy arrays into those calls and adds nothing else.
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import capi
+from .capi import (NOP_BC_REFLECTIVE, NOP_BC_VACUUM, NOP_GEOM_SLAB, NOP_GEOM_XY,
+                   NOP_PREC_F32, NOP_PREC_F64, NOP_WARM_NONE, NOP_WARM_RECAST, NopError)
+
+__all__ = ["Solver", "NopError", "capi"]
+
+
+def _opts(tol=1e-6, itmax=10000, precision=NOP_PREC_F32, tol_k=1e-7, tol_inner=None,
+          itmax_inner=10000, warm_start=NOP_WARM_NONE, recast_tol=1e-4, recast_itmax=200,
+          flags=0):
+    o = capi.nop_solve_opts()
+    o.tol, o.tol_k = tol, tol_k
+    o.tol_inner = tol if tol_inner is None else tol_inner
+    o.itmax, o.itmax_inner, o.precision = itmax, itmax_inner, precision
+    o.warm_start, o.recast_tol, o.recast_itmax, o.flags = warm_start, recast_tol, recast_itmax, flags
+    return o
+
+
+class Solver:
+    """One nop_ctx on one CUDA device."""
+
+    def __init__(self, device=0):
+        self._L = capi.lib()
+        h = C.c_void_p()
+        rc = self._L.nop_create(C.byref(h), device)
+        if rc != 0:
+            raise NopError(rc, "nop_create(device=%d)" % device)
+        self.h = h
+        self._keep = []
+        self.n_inst = 0
+        self.G = 0
+        self.C = 0
+
+    def close(self):
+        if self.h:
+            self._L.nop_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc != 0:
+            raise NopError(rc, "%s: %s" % (what, self._L.nop_last_error(self.h).decode()))
+        return rc
+
+    def set_stream(self, stream_handle):
+        self._check(self._L.nop_set_stream(self.h, C.c_void_p(stream_handle)), "nop_set_stream")
+
+    def set_timing(self, enable=True):
+        self._check(self._L.nop_set_timing(self.h, 1 if enable else 0), "nop_set_timing")
+
+    def timing(self):
+        t = capi.nop_timings()
+        self._check(self._L.nop_get_timing(self.h, C.byref(t)), "nop_get_timing")
+        return {k: getattr(t, k) for k, _ in t._fields_}
+
+    # ---------------------------------------------------------- problems
+    def set_slabs(self, n_cells, width, order, sigma_t, sigma_s, source=None,
+                  nu_sigma_f=None, chi=None, bc=(0, 0)):
+        """Batch of slabs; arrays group-major over all cells (see nop.h)."""
+        n_cells = np.ascontiguousarray(n_cells, dtype=np.int32)
+        order = np.ascontiguousarray(order, dtype=np.int32)
+        width = capi._f64(width)
+        G = int(np.asarray(sigma_t).size // int(n_cells.sum()))
+        arrs = [capi._f64(sigma_t), capi._f64(sigma_s),
+                None if source is None else capi._f64(source),
+                None if nu_sigma_f is None else capi._f64(nu_sigma_f),
+                None if chi is None else capi._f64(chi)]
+        p = capi.nop_problem()
+        p.geometry, p.n_inst = NOP_GEOM_SLAB, len(n_cells)
+        p.n_cells, p.width, p.order = capi._ptr(n_cells, capi._ip), capi._ptr(width), capi._ptr(order, capi._ip)
+        p.n_groups = G
+        p.sigma_t, p.sigma_s, p.source, p.nu_sigma_f, p.chi = [capi._ptr(a) for a in arrs]
+        p.bc[0], p.bc[1] = int(bc[0]), int(bc[1])
+        self._check(self._L.nop_set_problem(self.h, C.byref(p)), "nop_set_problem")
+        self.n_inst, self.G, self.C = len(n_cells), G, int(n_cells.sum())
+
+    def set_xy(self, nx, ny, lx, ly, sigma_t, sigma_s, source=None, nu_sigma_f=None,
+               chi=None, bc=(0, 0, 0, 0)):
+        G = int(np.asarray(sigma_t).size // (nx * ny))
+        arrs = [capi._f64(sigma_t), capi._f64(sigma_s),
+                None if source is None else capi._f64(source),
+                None if nu_sigma_f is None else capi._f64(nu_sigma_f),
+                None if chi is None else capi._f64(chi)]
+        order = np.array([8], dtype=np.int32)
+        p = capi.nop_problem()
+        p.geometry, p.n_inst, p.order = NOP_GEOM_XY, 1, capi._ptr(order, capi._ip)
+        p.nx, p.ny, p.lx, p.ly, p.n_groups = nx, ny, lx, ly, G
+        p.sigma_t, p.sigma_s, p.source, p.nu_sigma_f, p.chi = [capi._ptr(a) for a in arrs]
+        for f in range(4):
+            p.bc[f] = int(bc[f])
+        self._check(self._L.nop_set_problem(self.h, C.byref(p)), "nop_set_problem")
+        self.n_inst, self.G, self.C = 1, G, nx * ny
+
+    def quadrature(self, inst=0):
+        mu, eta, w = np.zeros(128), np.zeros(128), np.zeros(128)
+        n = C.c_int()
+        self._check(self._L.nop_get_quadrature(self.h, inst, capi._ptr(mu), capi._ptr(eta),
+                                               capi._ptr(w), C.byref(n)), "nop_get_quadrature")
+        k = n.value
+        return mu[:k], eta[:k], w[:k]
+
+    # ------------------------------------------------------------ solves
+    def _stats(self):
+        st = capi.nop_stats()
+        it = np.zeros(self.n_inst, dtype=np.int32)
+        ss = np.zeros(self.n_inst, dtype=np.int32)
+        st.inst_iterations, st.inst_status = capi._ptr(it, capi._ip), capi._ptr(ss, capi._ip)
+        return st, it, ss
+
+    def solve_fixed_source(self, phi0=None, check=True, **kw):
+        o = _opts(**kw)
+        phi = np.zeros(self.G * self.C)
+        p0 = None if phi0 is None else capi._f64(phi0)
+        st, it, ss = self._stats()
+        rc = self._L.nop_solve_fixed_source(self.h, C.byref(o),
+                                            None if p0 is None else p0.ctypes.data,
+                                            phi.ctypes.data, C.byref(st))
+        if check and rc not in (0, capi.NOP_ENOCONV):
+            self._check(rc, "nop_solve_fixed_source")
+        return phi, {"rc": rc, "iterations": it, "status": ss, "max_change": st.max_change,
+                     "recast_iterations": st.recast_iterations,
+                     "recast_status": st.recast_status}
+
+    def solve_fixed_source_dev(self, phi_out_ptr, phi0_ptr=None, **kw):
+        """Device-resident variant: phi_out_ptr (and phi0_ptr) are device pointers
+        to FP64 arrays of G*C entries; per-instance statistics come back to the host."""
+        flags = capi.NOP_OUT_DEVICE | (capi.NOP_PHI0_DEVICE if phi0_ptr else 0)
+        o = _opts(flags=flags, **kw)
+        st, it, ss = self._stats()
+        rc = self._L.nop_solve_fixed_source(self.h, C.byref(o), phi0_ptr, phi_out_ptr,
+                                            C.byref(st))
+        if rc not in (0, capi.NOP_ENOCONV):
+            self._check(rc, "nop_solve_fixed_source")
+        return {"rc": rc, "iterations": it, "status": ss,
+                "recast_iterations": st.recast_iterations, "recast_status": st.recast_status}
+
+    def solve_eigen(self, phi0=None, k0=0.0, check=True, **kw):
+        o = _opts(**kw)
+        phi = np.zeros(self.G * self.C)
+        k = np.zeros(self.n_inst)
+        p0 = None if phi0 is None else capi._f64(phi0)
+        st, it, ss = self._stats()
+        rc = self._L.nop_solve_eigen(self.h, C.byref(o), None if p0 is None else p0.ctypes.data,
+                                     float(k0), phi.ctypes.data, k.ctypes.data, C.byref(st))
+        if check and rc not in (0, capi.NOP_ENOCONV):
+            self._check(rc, "nop_solve_eigen")
+        return k, phi, {"rc": rc, "inner": it, "status": ss, "outer": st.max_outer,
+                        "max_change": st.max_change,
+                        "recast_iterations": st.recast_iterations}

@@ -1,0 +1,104 @@
+"""ctypes binding of libnop.so: the C ABI of include/nop.h under the same names.
+
+Argument marshalling only -- every computation happens in the CUDA library.
+Importing this module loads the in-tree library and fails loudly when it is
+missing; there is no fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnop.so")
+
+NOP_OK, NOP_EINVAL, NOP_ECUDA, NOP_ENOMEM = 0, -1, -2, -3
+NOP_ENOCONV, NOP_EDIVERGE, NOP_ETIMEOUT, NOP_ENAN, NOP_ESTATE = -4, -5, -6, -7, -8
+NOP_GEOM_SLAB, NOP_GEOM_XY = 1, 2
+NOP_BC_VACUUM, NOP_BC_REFLECTIVE = 0, 1
+NOP_PREC_F32, NOP_PREC_F64 = 0, 1
+NOP_WARM_NONE, NOP_WARM_RECAST = 0, 1
+NOP_PHI0_DEVICE, NOP_OUT_DEVICE = 1, 2
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+class nop_problem(C.Structure):
+    _fields_ = [("geometry", C.c_int), ("n_inst", C.c_int), ("n_cells", _ip),
+                ("width", _dp), ("order", _ip), ("nx", C.c_int), ("ny", C.c_int),
+                ("lx", C.c_double), ("ly", C.c_double), ("n_groups", C.c_int),
+                ("sigma_t", _dp), ("sigma_s", _dp), ("source", _dp),
+                ("nu_sigma_f", _dp), ("chi", _dp), ("bc", C.c_int * 4)]
+
+
+class nop_solve_opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("tol_k", C.c_double), ("tol_inner", C.c_double),
+                ("itmax", C.c_int), ("itmax_inner", C.c_int), ("precision", C.c_int),
+                ("warm_start", C.c_int), ("recast_tol", C.c_double),
+                ("recast_itmax", C.c_int), ("flags", C.c_int)]
+
+
+class nop_stats(C.Structure):
+    _fields_ = [("status", C.c_int), ("max_iterations", C.c_int),
+                ("sum_iterations", C.c_longlong), ("max_outer", C.c_int),
+                ("recast_iterations", C.c_int), ("recast_status", C.c_int),
+                ("max_change", C.c_double), ("inst_iterations", _ip),
+                ("inst_status", _ip)]
+
+
+class nop_timings(C.Structure):
+    _fields_ = [("sweep_ms", C.c_double), ("operator_ms", C.c_double),
+                ("setup_ms", C.c_double), ("launches", C.c_longlong),
+                ("sweep_launches", C.c_longlong), ("cell_angle_updates", C.c_double)]
+
+
+# every symbol include/nop.h declares, with its ctypes signature
+SIGNATURES = {
+    "nop_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int]),
+    "nop_destroy": (C.c_int, [C.c_void_p]),
+    "nop_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "nop_status_str": (C.c_char_p, [C.c_int]),
+    "nop_last_error": (C.c_char_p, [C.c_void_p]),
+    "nop_set_problem": (C.c_int, [C.c_void_p, C.POINTER(nop_problem)]),
+    "nop_get_quadrature": (C.c_int, [C.c_void_p, C.c_int, _dp, _dp, _dp, _ip]),
+    "nop_solve_fixed_source": (C.c_int, [C.c_void_p, C.POINTER(nop_solve_opts), C.c_void_p,
+                                         C.c_void_p, C.POINTER(nop_stats)]),
+    "nop_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "nop_get_timing": (C.c_int, [C.c_void_p, C.POINTER(nop_timings)]),
+    "nop_solve_eigen": (C.c_int, [C.c_void_p, C.POINTER(nop_solve_opts), C.c_void_p,
+                                  C.c_double, C.c_void_p, C.c_void_p,
+                                  C.POINTER(nop_stats)]),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libnop.so (built by paper_2509_01416_gb300.build) or raise."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libnop.so is not built (run __graft_entry__.build()); "
+                               "there is no CPU fallback")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class NopError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (lib().nop_status_str(code).decode(), code, msg))
+        self.code = code
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a, t=_dp):
+    return None if a is None else a.ctypes.data_as(t)

@@ -1,0 +1,400 @@
+// C ABI entry points: context lifecycle, problem upload, solve dispatch.
+#include <cmath>
+#include <cstring>
+#include <algorithm>
+#include <new>
+
+#include "nop_internal.cuh"
+
+int nop_ctx::scratch(const char* name, size_t bytes, void** out) {
+    if (bytes == 0) bytes = 16;
+    for (auto& kv : bufs) {
+        if (kv.first == name) {
+            if (kv.second.bytes >= bytes) {
+                *out = kv.second.p;
+                return NOP_OK;
+            }
+            cudaFree(kv.second.p);
+            kv.second.p = nullptr;
+            kv.second.bytes = 0;
+            cudaError_t e = cudaMalloc(&kv.second.p, bytes);
+            if (e != cudaSuccess) {
+                set_error(std::string("cudaMalloc ") + name + ": " + cudaGetErrorString(e));
+                return NOP_ENOMEM;
+            }
+            kv.second.bytes = bytes;
+            *out = kv.second.p;
+            return NOP_OK;
+        }
+    }
+    nop::DevBuf b;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        set_error(std::string("cudaMalloc ") + name + ": " + cudaGetErrorString(e));
+        return NOP_ENOMEM;
+    }
+    b.bytes = bytes;
+    bufs.emplace_back(name, b);
+    *out = b.p;
+    return NOP_OK;
+}
+
+int nop_ctx::phase_begin(int phase) {
+    if (!timing) return -1;
+    Mark m;
+    m.phase = phase;
+    for (cudaEvent_t* e : {&m.a, &m.b}) {
+        if (!event_pool.empty()) {
+            *e = event_pool.back();
+            event_pool.pop_back();
+        } else if (cudaEventCreate(e) != cudaSuccess) {
+            return -1;
+        }
+    }
+    cudaEventRecord(m.a, stream);
+    marks.push_back(m);
+    return (int)marks.size() - 1;
+}
+
+void nop_ctx::phase_end(int mark) {
+    if (mark < 0 || mark >= (int)marks.size()) return;
+    cudaEventRecord(marks[mark].b, stream);
+}
+
+namespace {
+
+int upload(nop_ctx* ctx, const char* name, const void* src, size_t bytes, void** dst) {
+    NOP_TRY(ctx->scratch(name, bytes, dst));
+    NOP_CUDA_TRY(ctx, cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    return NOP_OK;
+}
+
+bool finite_pos(const double* a, long long n) {
+    for (long long i = 0; i < n; ++i)
+        if (!(a[i] > 0.0) || !std::isfinite(a[i])) return false;
+    return true;
+}
+bool finite_all(const double* a, long long n) {
+    for (long long i = 0; i < n; ++i)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* nop_status_str(int s) {
+    switch (s) {
+        case NOP_OK: return "ok";
+        case NOP_EINVAL: return "invalid argument";
+        case NOP_ECUDA: return "CUDA error";
+        case NOP_ENOMEM: return "out of memory";
+        case NOP_ENOCONV: return "iteration cap reached";
+        case NOP_EDIVERGE: return "recast iteration diverged";
+        case NOP_ETIMEOUT: return "device wait limit reached";
+        case NOP_ENAN: return "non-finite value";
+        case NOP_ESTATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+const char* nop_last_error(nop_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int nop_create(nop_ctx** out, int device) {
+    if (!out) return NOP_EINVAL;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) return NOP_ECUDA;
+    nop_ctx* c = new (std::nothrow) nop_ctx();
+    if (!c) return NOP_ENOMEM;
+    c->device = device;
+    if (cudaSetDevice(device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device) !=
+            cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return NOP_ECUDA;
+    }
+    c->stream = c->own_stream;
+    *out = c;
+    return NOP_OK;
+}
+
+int nop_destroy(nop_ctx* ctx) {
+    if (!ctx) return NOP_OK;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& m : ctx->marks) {
+        cudaEventDestroy(m.a);
+        cudaEventDestroy(m.b);
+    }
+    for (auto e : ctx->event_pool) cudaEventDestroy(e);
+    for (auto& kv : ctx->bufs) cudaFree(kv.second.p);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    delete ctx;
+    return NOP_OK;
+}
+
+int nop_set_stream(nop_ctx* ctx, void* stream) {
+    if (!ctx) return NOP_EINVAL;
+    ctx->stream = stream ? (cudaStream_t)stream : ctx->own_stream;
+    return NOP_OK;
+}
+
+int nop_set_timing(nop_ctx* ctx, int enable) {
+    if (!ctx) return NOP_EINVAL;
+    NOP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    for (auto& m : ctx->marks) {
+        ctx->event_pool.push_back(m.a);
+        ctx->event_pool.push_back(m.b);
+    }
+    ctx->marks.clear();
+    ctx->launches = ctx->sweep_launches = 0;
+    ctx->cell_angle_updates = 0;
+    ctx->timing = enable != 0;
+    return NOP_OK;
+}
+
+int nop_get_timing(nop_ctx* ctx, nop_timings* out) {
+    if (!ctx || !out) return NOP_EINVAL;
+    NOP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    double ms[3] = {0, 0, 0};
+    for (auto& m : ctx->marks) {
+        float t = 0;
+        if (cudaEventElapsedTime(&t, m.a, m.b) == cudaSuccess) ms[m.phase] += t;
+    }
+    out->sweep_ms = ms[0];
+    out->operator_ms = ms[1];
+    out->setup_ms = ms[2];
+    out->launches = ctx->launches;
+    out->sweep_launches = ctx->sweep_launches;
+    out->cell_angle_updates = ctx->cell_angle_updates;
+    return NOP_OK;
+}
+
+int nop_set_problem(nop_ctx* ctx, const nop_problem* p) {
+    if (!ctx || !p) return NOP_EINVAL;
+    NOP_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    ctx->has_problem = false;
+    const int G = p->n_groups;
+    if (G < 1 || G > 64) {
+        ctx->set_error("n_groups must be in 1..64");
+        return NOP_EINVAL;
+    }
+    if (!p->sigma_t || !p->sigma_s || !p->order) {
+        ctx->set_error("sigma_t, sigma_s and order are required");
+        return NOP_EINVAL;
+    }
+    const bool fixed = p->source != nullptr;
+    const bool fiss = p->nu_sigma_f != nullptr;
+    if (fiss && !p->chi) {
+        ctx->set_error("chi is required with nu_sigma_f");
+        return NOP_EINVAL;
+    }
+    long long C = 0;
+    if (p->geometry == NOP_GEOM_SLAB) {
+        if (p->n_inst < 1 || !p->n_cells || !p->width) {
+            ctx->set_error("slab batch needs n_inst >= 1, n_cells and width");
+            return NOP_EINVAL;
+        }
+        for (int b = 0; b < p->n_inst; ++b) {
+            if (p->n_cells[b] < 1 || !(p->width[b] > 0) || p->order[b] < 2 ||
+                p->order[b] > 128 || (p->order[b] & 1)) {
+                ctx->set_error("slab instance " + std::to_string(b) +
+                               ": need n_cells >= 1, width > 0, even order in 2..128");
+                return NOP_EINVAL;
+            }
+            C += p->n_cells[b];
+        }
+    } else if (p->geometry == NOP_GEOM_XY) {
+        if (p->n_inst != 1 || p->nx < 1 || p->ny < 1 || !(p->lx > 0) || !(p->ly > 0) ||
+            p->order[0] != 8) {
+            ctx->set_error("x-y problem needs n_inst = 1, nx, ny >= 1, lx, ly > 0, order 8");
+            return NOP_EINVAL;
+        }
+        C = (long long)p->nx * p->ny;
+    } else {
+        ctx->set_error("unknown geometry");
+        return NOP_EINVAL;
+    }
+    for (int f = 0; f < 4; ++f)
+        if (p->bc[f] != NOP_BC_VACUUM && p->bc[f] != NOP_BC_REFLECTIVE) {
+            ctx->set_error("boundary condition must be vacuum or reflective");
+            return NOP_EINVAL;
+        }
+    if (!finite_pos(p->sigma_t, (long long)G * C) ||
+        !finite_all(p->sigma_s, (long long)G * G * C) ||
+        (fixed && !finite_all(p->source, (long long)G * C)) ||
+        (fiss && !finite_all(p->nu_sigma_f, (long long)G * C))) {
+        ctx->set_error("coefficients must be finite and sigma_t > 0");
+        return NOP_EINVAL;
+    }
+    ctx->geometry = p->geometry;
+    ctx->G = G;
+    ctx->C = C;
+    ctx->has_source = fixed;
+    ctx->has_fission = fiss;
+    for (int f = 0; f < 4; ++f) ctx->bc[f] = p->bc[f];
+    void* d;
+    NOP_TRY(upload(ctx, "sigt", p->sigma_t, sizeof(double) * G * C, &d));
+    ctx->sigt_d = (double*)d;
+    NOP_TRY(upload(ctx, "sigs", p->sigma_s, sizeof(double) * G * G * C, &d));
+    ctx->sigs_d = (double*)d;
+    ctx->src_d = nullptr;
+    ctx->nsf_d = nullptr;
+    ctx->chi_d = nullptr;
+    if (fixed) {
+        NOP_TRY(upload(ctx, "src", p->source, sizeof(double) * G * C, &d));
+        ctx->src_d = (double*)d;
+    }
+    if (fiss) {
+        NOP_TRY(upload(ctx, "nsf", p->nu_sigma_f, sizeof(double) * G * C, &d));
+        ctx->nsf_d = (double*)d;
+        NOP_TRY(upload(ctx, "chi", p->chi, sizeof(double) * G, &d));
+        ctx->chi_d = (double*)d;
+    }
+    if (p->geometry == NOP_GEOM_SLAB) {
+        nop::SlabDev& s = ctx->slab;
+        const int B = p->n_inst;
+        s.n_inst = B;
+        s.C = C;
+        s.ncell.assign(p->n_cells, p->n_cells + B);
+        s.order.assign(p->order, p->order + B);
+        s.width.assign(p->width, p->width + B);
+        s.cell_off.resize(B);
+        std::vector<double> dx(B);
+        std::vector<long long> boff(B);
+        long long o = 0, bo = 0;
+        for (int b = 0; b < B; ++b) {
+            s.cell_off[b] = o;
+            o += s.ncell[b];
+            dx[b] = s.width[b] / s.ncell[b];
+            boff[b] = bo;
+            bo += (long long)G * s.order[b];
+        }
+        s.bnd_total = bo;
+        s.cmax.assign(B, 0.0);
+        for (int b = 0; b < B; ++b)
+            for (int g = 0; g < G; ++g)
+                for (long long c = s.cell_off[b]; c < s.cell_off[b] + s.ncell[b]; ++c) {
+                    const double r = p->sigma_s[((long long)g * G + g) * C + c] /
+                                     p->sigma_t[(long long)g * C + c];
+                    s.cmax[b] = std::max(s.cmax[b], r);
+                }
+        NOP_TRY(upload(ctx, "cell_off", s.cell_off.data(), sizeof(long long) * B, &d));
+        s.cell_off_d = (long long*)d;
+        NOP_TRY(upload(ctx, "ncell", s.ncell.data(), sizeof(int) * B, &d));
+        s.ncell_d = (int*)d;
+        NOP_TRY(upload(ctx, "nang", s.order.data(), sizeof(int) * B, &d));
+        s.nang_d = (int*)d;
+        NOP_TRY(upload(ctx, "dx", dx.data(), sizeof(double) * B, &d));
+        s.dx_d = (double*)d;
+        NOP_TRY(upload(ctx, "boff", boff.data(), sizeof(long long) * B, &d));
+        s.boff_d = (long long*)d;
+        NOP_TRY(nop::build_gauss_legendre(ctx));   // synchronises the stream
+    } else {
+        ctx->xy.nx = p->nx;
+        ctx->xy.ny = p->ny;
+        ctx->xy.lx = p->lx;
+        ctx->xy.ly = p->ly;
+        NOP_TRY(nop::build_level_symmetric_s8(ctx));
+        NOP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    ctx->has_problem = true;
+    return NOP_OK;
+}
+
+int nop_get_quadrature(nop_ctx* ctx, int inst, double* mu, double* eta, double* w,
+                       int* n_out) {
+    if (!ctx || !mu || !w || !n_out) return NOP_EINVAL;
+    if (!ctx->has_problem) return NOP_ESTATE;
+    if (ctx->geometry == NOP_GEOM_SLAB) {
+        if (inst < 0 || inst >= ctx->slab.n_inst) return NOP_EINVAL;
+        const int N = ctx->slab.order[inst], q = ctx->slab.qoff_h[inst];
+        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(mu, ctx->slab.mu_d + q, sizeof(double) * N,
+                                          cudaMemcpyDeviceToHost, ctx->stream));
+        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(w, ctx->slab.w_d + q, sizeof(double) * N,
+                                          cudaMemcpyDeviceToHost, ctx->stream));
+        *n_out = N;
+    } else {
+        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(mu, ctx->xy.mu_d, sizeof(double) * 40,
+                                          cudaMemcpyDeviceToHost, ctx->stream));
+        if (eta)
+            NOP_CUDA_TRY(ctx, cudaMemcpyAsync(eta, ctx->xy.eta_d, sizeof(double) * 40,
+                                              cudaMemcpyDeviceToHost, ctx->stream));
+        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(w, ctx->xy.w_d, sizeof(double) * 40,
+                                          cudaMemcpyDeviceToHost, ctx->stream));
+        *n_out = 40;
+    }
+    NOP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return NOP_OK;
+}
+
+static int check_opts(nop_ctx* ctx, const nop_solve_opts* o, bool eigen) {
+    if (!o) return NOP_EINVAL;
+    if (!(o->tol > 0) || o->itmax < 1 || (o->precision != NOP_PREC_F32 &&
+                                          o->precision != NOP_PREC_F64)) {
+        ctx->set_error("need tol > 0, itmax >= 1 and a known precision");
+        return NOP_EINVAL;
+    }
+    if (eigen && (!(o->tol_k > 0) || !(o->tol_inner > 0) || o->itmax_inner < 1)) {
+        ctx->set_error("eigen solve needs tol_k, tol_inner > 0 and itmax_inner >= 1");
+        return NOP_EINVAL;
+    }
+    return NOP_OK;
+}
+
+int nop_solve_fixed_source(nop_ctx* ctx, const nop_solve_opts* o, const double* phi0,
+                           double* phi_out, nop_stats* st) {
+    if (!ctx) return NOP_EINVAL;
+    NOP_TRY(check_opts(ctx, o, false));
+    if (!ctx->has_problem || !ctx->has_source) {
+        ctx->set_error("fixed-source solve needs a problem with a source");
+        return NOP_ESTATE;
+    }
+    NOP_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    if (st) {
+        st->recast_iterations = 0;
+        st->recast_status = NOP_OK;
+    }
+    if (o->warm_start != NOP_WARM_NONE) {
+        ctx->set_error("warm start requested but no neural operator is loaded");
+        return NOP_ESTATE;
+    }
+    if (ctx->geometry == NOP_GEOM_SLAB)
+        return nop::sn1d_solve(ctx, o, false, phi0, (o->flags & NOP_PHI0_DEVICE) != 0,
+                               nullptr, phi_out, (o->flags & NOP_OUT_DEVICE) != 0,
+                               nullptr, st);
+    ctx->set_error("x-y solver not available");
+    return NOP_EINVAL;
+}
+
+int nop_solve_eigen(nop_ctx* ctx, const nop_solve_opts* o, const double* phi0, double k0,
+                    double* phi_out, double* k_out, nop_stats* st) {
+    if (!ctx) return NOP_EINVAL;
+    NOP_TRY(check_opts(ctx, o, true));
+    if (!ctx->has_problem || !ctx->has_fission) {
+        ctx->set_error("eigen solve needs a problem with nu_sigma_f and chi");
+        return NOP_ESTATE;
+    }
+    NOP_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    if (st) {
+        st->recast_iterations = 0;
+        st->recast_status = NOP_OK;
+    }
+    if (o->warm_start != NOP_WARM_NONE) {
+        ctx->set_error("warm start requested but no neural operator is loaded");
+        return NOP_ESTATE;
+    }
+    if (ctx->geometry == NOP_GEOM_SLAB) {
+        std::vector<double> k0v(ctx->slab.n_inst, k0 > 0 ? k0 : 1.0);
+        return nop::sn1d_solve(ctx, o, true, phi0, (o->flags & NOP_PHI0_DEVICE) != 0,
+                               k0v.data(), phi_out, (o->flags & NOP_OUT_DEVICE) != 0, k_out,
+                               st);
+    }
+    ctx->set_error("x-y solver not available");
+    return NOP_EINVAL;
+}
+
+}  // extern "C"

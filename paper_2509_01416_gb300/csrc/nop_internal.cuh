@@ -1,0 +1,125 @@
+// Internal declarations of the GB300 S_N / MD-PNOP library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/nop.h"
+
+namespace nop {
+
+// Status of one CUDA call; records the message on the context and returns.
+#define NOP_CUDA_TRY(ctx, call)                                                   \
+    do {                                                                          \
+        cudaError_t e_ = (call);                                                  \
+        if (e_ != cudaSuccess) {                                                  \
+            (ctx)->set_error(std::string(#call) + ": " + cudaGetErrorString(e_)); \
+            return NOP_ECUDA;                                                     \
+        }                                                                         \
+    } while (0)
+
+#define NOP_TRY(expr)              \
+    do {                           \
+        int r_ = (expr);           \
+        if (r_ != NOP_OK) return r_; \
+    } while (0)
+
+// A device allocation that only grows.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// Problem state of a 1D slab batch (device side unless noted).
+struct SlabDev {
+    int n_inst = 0;
+    long long C = 0;                 // total cells
+    std::vector<int> ncell, order;   // host copies
+    std::vector<double> width;
+    std::vector<double> cmax;        // host: largest in-group scattering ratio
+    std::vector<long long> cell_off; // host prefix sums
+    long long* cell_off_d = nullptr;
+    int* ncell_d = nullptr;
+    int* nang_d = nullptr;
+    double* dx_d = nullptr;
+    int* qoff_d = nullptr;           // offset of the instance's nodes in mu_d/w_d
+    long long* boff_d = nullptr;     // offset of the instance's boundary fluxes
+    long long bnd_total = 0;
+    double* mu_d = nullptr;          // Gauss-Legendre nodes, one block per distinct order
+    double* w_d = nullptr;
+    std::vector<int> qoff_h;
+};
+
+struct XYDev {
+    int nx = 0, ny = 0;
+    double lx = 0, ly = 0;
+    double* mu_d = nullptr;          // 40 directions
+    double* eta_d = nullptr;
+    double* w_d = nullptr;
+};
+
+}  // namespace nop
+
+struct nop_ctx {
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    std::string err;
+
+    // problem
+    bool has_problem = false;
+    int geometry = 0;
+    int G = 0;
+    bool has_source = false, has_fission = false;
+    int bc[4] = {0, 0, 0, 0};
+    nop::SlabDev slab;
+    nop::XYDev xy;
+    long long C = 0;
+    // FP64 originals
+    double *sigt_d = nullptr, *sigs_d = nullptr, *src_d = nullptr, *nsf_d = nullptr,
+           *chi_d = nullptr;
+
+    // phase timing (nop_set_timing)
+    bool timing = false;
+    struct Mark {
+        int phase;                 // 0 sweep, 1 operator, 2 setup
+        cudaEvent_t a, b;
+    };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> event_pool;
+    long long launches = 0, sweep_launches = 0;
+    double cell_angle_updates = 0;
+    // Open a timed phase on the stream; returns the mark index or -1.
+    int phase_begin(int phase);
+    void phase_end(int mark);
+    void count_launch(bool sweep) {
+        if (timing) {
+            ++launches;
+            if (sweep) ++sweep_launches;
+        }
+    }
+
+    // scratch owned by the solvers (named buffers)
+    std::vector<std::pair<std::string, nop::DevBuf>> bufs;
+
+    void set_error(const std::string& m) { err = m; }
+    // Device buffer `name` with at least `bytes` bytes (grows, contents kept undefined).
+    int scratch(const char* name, size_t bytes, void** out);
+};
+
+namespace nop {
+// Quadrature builders (quadrature.cu)
+int build_gauss_legendre(nop_ctx* ctx);
+int build_level_symmetric_s8(nop_ctx* ctx);
+
+// 1D slab solvers (sn1d.cu)
+int sn1d_solve(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* phi0,
+               bool phi0_dev, const double* k0, double* phi_out, bool out_dev,
+               double* k_out, nop_stats* st);
+
+// Autotuner for the 1D sweep: lanes per angle group (log2) and angles per lane.
+void sn1d_pick_config(int cells, int order, int* lg_ng, int* A);
+}  // namespace nop

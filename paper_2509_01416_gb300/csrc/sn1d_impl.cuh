@@ -1,0 +1,799 @@
+// Batched 1D slab S_N solver: source iteration (Sec. 3.1 Eq. 3a/4b, Sec. 5.1
+// Eq. 12 and 20) and power iteration with inner sweeps (Sec. 5.2 Eq. 26,
+// App. A2 Eq. A2-A4), multigroup by Gauss-Seidel over groups (Sec. 5.3
+// Eq. 27-29), diamond-difference spatial closure.
+//
+// GPU organisation.  One warp owns one slab instance at a time and runs its
+// whole iteration (all sweeps, norms, eigenvalue updates) without leaving the
+// kernel; warps pull instances from a work counter in longest-first order.
+// The 32 lanes are split into nt = 32/ng cell chunks x ng angle groups; a lane
+// carries A polar angles |mu| of its group over its chunk, first for mu < 0
+// (right to left) and then for mu > 0 (left to right).  Along the cells the
+// diamond-difference recurrence is affine, psi_out = alpha psi_in + beta with
+// alpha = (c - st)/(c + st), beta = 2 s/(c + st), c = 2|mu|/dx, so chunks first
+// compose their maps, exchange them in a warp-shuffle scan, and then sweep with
+// the correct incoming flux.  The angle sum phi_i = sum w psi_i is reduced over
+// the ng lanes of a chunk with xor shuffles; the lane (i mod ng) owns cell i.
+//
+// Per-cell working data (arrays of the whole batch, group-major):
+//   X[g][c] = {st, ss/2 (in-group scattering), z (half the source from outside
+//              the group's own flux), phi}
+//   U[g][c] = {s (emission density used this iteration), phi_minus}
+// Norms, eigenvalue ratios and convergence tests are FP64 in every precision.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#pragma once
+#include "nop_internal.cuh"
+
+#define SN1D_THREADS 256
+#define SN1D_BLOCKS_PER_SM 4
+#define SN1D_SMEM_BYTES (48 * 1024)
+
+namespace nop {
+
+template <typename T>
+struct alignas(4 * sizeof(T)) Cell4 {
+    T st, y, z, phi;
+};
+template <typename T>
+struct alignas(2 * sizeof(T)) Cell2 {
+    T s, pm;
+};
+
+struct Sn1dArgs {
+    int n_inst;
+    int G;
+    long long C;
+    const int* order_list;   // small instances (one warp each), longest first
+    int n_small;
+    const int* big_list;     // large instances (one whole block each), longest first
+    int n_big;
+    int* counter;            // [0] small queue, [1] big queue
+    const long long* cell_off;
+    const int* ncell;
+    const int* nang;
+    const double* dx;
+    const int* qoff;
+    const double* mu;
+    const double* w;
+    const long long* boff;
+    const int* cfg;
+    void* X;
+    void* U;
+    const void* scat;     // T [G][G][C], halved; only read when G > 1
+    void* ext;            // T [G][C], halved external / fission source
+    void* psib;           // T boundary fluxes [boff + (g*h + hi)*2 + side]
+    int bc_left, bc_right;
+    int smem_cells;       // cells the block path can stage in shared memory
+    // eigen
+    int eigen;
+    const void* nsf;      // T [G][C]
+    const double* chi;    // [G]
+    void* phiprev;        // T [G][C]
+    const double* k0;     // [n_inst]
+    double tol, tol_inner, tol_k;
+    int itmax, itmax_inner;
+    // outputs
+    int* it_out;
+    int* st_out;
+    double* ch_out;
+    double* k_out;
+    int* outer_out;
+};
+
+// Reciprocal for the DD cell solve.  FP32: the special-function unit's
+// approximation refined by one Newton step, e = 1 - d r, r <- r + r e, which
+// removes the approximation's bias (a biased reciprocal scales every sweep and
+// shifts eigenvalues by ~bias/(1 - spectral radius)).
+__device__ __forceinline__ float rcp_dd(float d) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+    const float e = fmaf(-d, r, 1.0f);
+    return fmaf(r, e, r);
+}
+__device__ __forceinline__ double rcp_dd(double d) { return 1.0 / d; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// The threads that own one instance: one warp, or the whole block.
+struct Grp {
+    bool block;
+    int rank, size, warp, nwarps;
+    double* red;   // block reduction scratch (nwarps doubles)
+    __device__ void sync() const {
+        if (block) __syncthreads();
+        else __syncwarp();
+    }
+    __device__ double sum(double v) const {
+        v = warp_sum(v);
+        if (!block) return v;
+        if ((threadIdx.x & 31) == 0) red[warp] = v;
+        __syncthreads();
+        double t = 0.0;
+        for (int k = 0; k < nwarps; ++k) t += red[k];
+        __syncthreads();
+        return t;
+    }
+};
+
+// Shared-memory staging of the block path: source, and the two half-range
+// angle sums of every cell.
+template <typename T>
+struct Stage {
+    T* s;
+    T* pm;
+    T* pp;
+};
+
+// One direction half (MINUS: mu < 0, cells right to left) of one group, for
+// the angles this warp carries.  Warp path: the owner lane stores the MINUS
+// partial sum in U and completes the cell in the PLUS half.  Block path: the
+// source comes from shared memory and owners add their partial sums there.
+template <typename T, int A, bool MINUS, bool BLOCK>
+__device__ __forceinline__ void sweep_half(Cell4<T>* X, Cell2<T>* U, const Stage<T>& sg, int I,
+                                           int lg, const T (&cc)[A], const T (&wt)[A],
+                                           const T (&psi_bnd)[A], T (&psi_out)[A],
+                                           double& acc_d, double& acc_n) {
+    const int lane = threadIdx.x & 31;
+    const int ng = 1 << lg, nt = 32 >> lg;
+    const int j = lane & (ng - 1), t = lane >> lg;
+    const int m = (I + nt - 1) / nt;
+    const int k0 = t * m;
+    const int len = max(0, min(m, I - k0));
+    T psi[A];
+#pragma unroll
+    for (int q = 0; q < A; ++q) psi[q] = psi_bnd[q];
+    if (nt > 1) {
+        T Ac[A], Bc[A];
+#pragma unroll
+        for (int q = 0; q < A; ++q) {
+            Ac[q] = T(1);
+            Bc[q] = T(0);
+        }
+        for (int k = 0; k < len; ++k) {
+            const int i = MINUS ? (I - 1 - (k0 + k)) : (k0 + k);
+            T st, s;
+            if (BLOCK) {
+                st = X[i].st;
+                s = sg.s[i];
+            } else {
+                const Cell4<T> v = X[i];
+                st = v.st;
+                s = MINUS ? (v.y * v.phi + v.z) : U[i].s;
+            }
+#pragma unroll
+            for (int q = 0; q < A; ++q) {
+                const T r = rcp_dd(cc[q] + st);
+                const T al = (cc[q] - st) * r;
+                Bc[q] = al * Bc[q] + T(2) * s * r;
+                Ac[q] = al * Ac[q];
+            }
+        }
+        // inclusive scan of the chunk maps along the sweep (lanes stride ng)
+        for (int d = 1; d < nt; d <<= 1) {
+#pragma unroll
+            for (int q = 0; q < A; ++q) {
+                const T Ao = __shfl_up_sync(0xffffffffu, Ac[q], d << lg);
+                const T Bo = __shfl_up_sync(0xffffffffu, Bc[q], d << lg);
+                if (t >= d) {
+                    Bc[q] = Ac[q] * Bo + Bc[q];
+                    Ac[q] = Ac[q] * Ao;
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < A; ++q) {
+            T Ae = __shfl_up_sync(0xffffffffu, Ac[q], ng);
+            T Be = __shfl_up_sync(0xffffffffu, Bc[q], ng);
+            if (t == 0) {
+                Ae = T(1);
+                Be = T(0);
+            }
+            psi[q] = Ae * psi_bnd[q] + Be;
+        }
+    }
+#pragma unroll 2
+    for (int k = 0; k < m; ++k) {
+        const bool valid = k < len;
+        const int i = MINUS ? (I - 1 - (k0 + k)) : (k0 + k);
+        T p = T(0), s = T(0), phio = T(0);
+        if (valid) {
+            T st;
+            if (BLOCK) {
+                st = X[i].st;
+                s = sg.s[i];
+            } else {
+                const Cell4<T> v = X[i];
+                st = v.st;
+                phio = v.phi;
+                s = MINUS ? (v.y * v.phi + v.z) : U[i].s;
+            }
+#pragma unroll
+            for (int q = 0; q < A; ++q) {
+                const T r = rcp_dd(cc[q] + st);
+                const T pc = (s + cc[q] * psi[q]) * r;
+                psi[q] = T(2) * pc - psi[q];
+                p += wt[q] * pc;
+            }
+        }
+        for (int o = 1; o < ng; o <<= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+        if (valid && (k & (ng - 1)) == j) {
+            if (BLOCK) {
+                atomicAdd(MINUS ? &sg.pm[i] : &sg.pp[i], p);
+            } else if (MINUS) {
+                Cell2<T> u;
+                u.s = s;
+                u.pm = p;
+                U[i] = u;
+            } else {
+                const T phin = p + U[i].pm;
+                const double df = (double)phin - (double)phio;
+                acc_d += df * df;
+                acc_n += (double)phin * (double)phin;
+                X[i].phi = phin;
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < A; ++q)
+        psi_out[q] = __shfl_sync(0xffffffffu, psi[q], ((nt - 1) << lg) + j);
+}
+
+// Out-of-group source of group g: z = ext/2 + sum_{g' != g} ss(g'->g)/2 phi_g'.
+template <typename T>
+__device__ void group_source(const Sn1dArgs& a, const Grp& gr, long long off, int I, int g) {
+    Cell4<T>* X = (Cell4<T>*)a.X;
+    const T* S = (const T*)a.scat;
+    const T* E = (const T*)a.ext;
+    for (int i = gr.rank; i < I; i += gr.size) {
+        const long long c = off + i;
+        T z = E[(long long)g * a.C + c];
+        for (int gp = 0; gp < a.G; ++gp)
+            if (gp != g) z += S[((long long)gp * a.G + g) * a.C + c] * X[(long long)gp * a.C + c].phi;
+        X[(long long)g * a.C + c].z = z;
+    }
+}
+
+// One source iteration over all groups; returns the relative L2 change.
+// `hb`/`hw`: this warp's slice of the half-angle range (the whole range on
+// the warp path).
+template <typename T, int A, bool BLOCK>
+__device__ double si_iteration(const Sn1dArgs& a, const Grp& gr, const Stage<T>& sg, int inst,
+                               long long off, int I, int h, int hb, int he, int lg,
+                               const T (&cc)[A], const T (&wt)[A]) {
+    const int lane = threadIdx.x & 31;
+    const int j = lane & ((1 << lg) - 1);
+    T* PB = (T*)a.psib + a.boff[inst];
+    double acc_d = 0.0, acc_n = 0.0;
+    for (int g = 0; g < a.G; ++g) {
+        if (a.G > 1) {
+            group_source<T>(a, gr, off, I, g);
+            gr.sync();
+        }
+        Cell4<T>* X = (Cell4<T>*)a.X + (long long)g * a.C + off;
+        Cell2<T>* U = (Cell2<T>*)a.U + (long long)g * a.C + off;
+        if (BLOCK) {
+            for (int i = gr.rank; i < I; i += gr.size) {
+                const Cell4<T> v = X[i];
+                sg.s[i] = v.y * v.phi + v.z;
+                sg.pm[i] = T(0);
+                sg.pp[i] = T(0);
+            }
+            gr.sync();
+        }
+        T bnd[A], out[A];
+        // mu < 0 enters at x = L: vacuum, or the mirror's latest outgoing flux
+#pragma unroll
+        for (int q = 0; q < A; ++q) {
+            const int hi = hb + j * A + q;
+            bnd[q] = (a.bc_right && hi < he) ? PB[(g * h + hi) * 2 + 1] : T(0);
+        }
+        sweep_half<T, A, true, BLOCK>(X, U, sg, I, lg, cc, wt, bnd, out, acc_d, acc_n);
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < A; ++q) {
+            const int hi = hb + j * A + q;
+            if (hi < he && (lane >> lg) == 0) PB[(g * h + hi) * 2 + 0] = out[q];
+            bnd[q] = a.bc_left ? out[q] : T(0);
+        }
+        sweep_half<T, A, false, BLOCK>(X, U, sg, I, lg, cc, wt, bnd, out, acc_d, acc_n);
+#pragma unroll
+        for (int q = 0; q < A; ++q) {
+            const int hi = hb + j * A + q;
+            if (hi < he && (lane >> lg) == 0) PB[(g * h + hi) * 2 + 1] = out[q];
+        }
+        gr.sync();
+        if (BLOCK) {
+            for (int i = gr.rank; i < I; i += gr.size) {
+                const T phin = sg.pm[i] + sg.pp[i];
+                const double df = (double)phin - (double)X[i].phi;
+                acc_d += df * df;
+                acc_n += (double)phin * (double)phin;
+                X[i].phi = phin;
+            }
+            gr.sync();
+        }
+    }
+    acc_d = gr.sum(acc_d);
+    acc_n = gr.sum(acc_n);
+    return acc_n > 0.0 ? sqrt(acc_d / acc_n) : (acc_d > 0.0 ? INFINITY : 0.0);
+}
+
+// production integral sum nsf * phi * dx over the instance (FP64)
+template <typename T>
+__device__ double production(const Sn1dArgs& a, const Grp& gr, long long off, int I, double dx) {
+    const Cell4<T>* X = (const Cell4<T>*)a.X;
+    const T* F = (const T*)a.nsf;
+    double acc = 0.0;
+    for (int g = 0; g < a.G; ++g)
+        for (int i = gr.rank; i < I; i += gr.size) {
+            const long long c = (long long)g * a.C + off + i;
+            acc += (double)F[c] * (double)X[c].phi;
+        }
+    return gr.sum(acc) * dx;
+}
+
+template <typename T, int A, bool BLOCK>
+__device__ void solve_instance(const Sn1dArgs& a, const Grp& gr, const Stage<T>& sg, int inst,
+                               int lg) {
+    const int lane = threadIdx.x & 31;
+    const int ng = 1 << lg;
+    const int j = lane & (ng - 1);
+    const int I = a.ncell[inst];
+    const int N = a.nang[inst];
+    const int h = N / 2;
+    // this warp's slice of the half-angle range
+    const int hw = BLOCK ? (h + gr.nwarps - 1) / gr.nwarps : h;
+    const int hb = BLOCK ? min(h, gr.warp * hw) : 0;
+    const int he = BLOCK ? min(h, hb + hw) : h;
+    const double dxv = a.dx[inst];
+    const long long off = a.cell_off[inst];
+    const int q0 = a.qoff[inst];
+    T cc[A], wt[A];
+#pragma unroll
+    for (int q = 0; q < A; ++q) {
+        const int hi = hb + j * A + q;
+        if (hi < he) {
+            cc[q] = (T)(2.0 * a.mu[q0 + h + hi] / dxv);
+            wt[q] = (T)a.w[q0 + h + hi];
+        } else {
+            cc[q] = T(1);
+            wt[q] = T(0);
+        }
+    }
+    T* PB = (T*)a.psib + a.boff[inst];
+    for (int e = gr.rank; e < a.G * N; e += gr.size) PB[e] = T(0);
+    gr.sync();
+
+    int status = NOP_OK;
+    double change = 0.0;
+    if (!a.eigen) {
+        int it = 0;
+        for (it = 1; it <= a.itmax; ++it) {
+            change = si_iteration<T, A, BLOCK>(a, gr, sg, inst, off, I, h, hb, he, lg, cc, wt);
+            if (!isfinite(change)) {
+                status = NOP_ENAN;
+                break;
+            }
+            if (change <= a.tol) break;
+        }
+        if (it > a.itmax) {
+            it = a.itmax;
+            status = NOP_ENOCONV;
+        }
+        if (gr.rank == 0) {
+            a.it_out[inst] = it;
+            a.st_out[inst] = status;
+            a.ch_out[inst] = change;
+        }
+        gr.sync();
+        return;
+    }
+
+    // ---- power iteration (App. A2): flux normalised to unit production
+    Cell4<T>* X = (Cell4<T>*)a.X;
+    T* PP = (T*)a.phiprev;
+    const T* F = (const T*)a.nsf;
+    T* E = (T*)a.ext;
+    double k = a.k0[inst];
+    double P = production<T>(a, gr, off, I, dxv);
+    if (!(P > 0.0) || !isfinite(P)) status = NOP_ENAN;
+    if (status == NOP_OK) {
+        const T sc = (T)(1.0 / P);
+        for (int g = 0; g < a.G; ++g)
+            for (int i = gr.rank; i < I; i += gr.size) X[(long long)g * a.C + off + i].phi *= sc;
+    }
+    gr.sync();
+    int inner_total = 0, n = 0;
+    double dk = INFINITY, dphi = INFINITY;
+    for (n = 1; n <= a.itmax && status == NOP_OK; ++n) {
+        // frozen fission source chi_g F / k (halved) and the previous flux
+        for (int i = gr.rank; i < I; i += gr.size) {
+            double Fi = 0.0;
+            for (int g = 0; g < a.G; ++g) {
+                const long long c = (long long)g * a.C + off + i;
+                Fi += (double)F[c] * (double)X[c].phi;
+                PP[c] = X[c].phi;
+            }
+            for (int g = 0; g < a.G; ++g) {
+                const long long c = (long long)g * a.C + off + i;
+                const T e = (T)(0.5 * a.chi[g] * Fi / k);
+                E[c] = e;
+                if (a.G == 1) X[c].z = e;
+            }
+        }
+        gr.sync();
+        int it;
+        for (it = 1; it <= a.itmax_inner; ++it) {
+            change = si_iteration<T, A, BLOCK>(a, gr, sg, inst, off, I, h, hb, he, lg, cc, wt);
+            if (!isfinite(change)) {
+                status = NOP_ENAN;
+                break;
+            }
+            if (change <= a.tol_inner) break;
+        }
+        inner_total += min(it, a.itmax_inner);
+        if (status != NOP_OK) break;
+        P = production<T>(a, gr, off, I, dxv);
+        if (!(P > 0.0) || !isfinite(P)) {
+            status = NOP_ENAN;
+            break;
+        }
+        const double kn = k * P;
+        const T sc = (T)(1.0 / P);
+        double d2 = 0.0, n2 = 0.0;
+        for (int g = 0; g < a.G; ++g)
+            for (int i = gr.rank; i < I; i += gr.size) {
+                const long long c = (long long)g * a.C + off + i;
+                const T v = X[c].phi * sc;
+                X[c].phi = v;
+                const double df = (double)v - (double)PP[c];
+                d2 += df * df;
+                n2 += (double)v * (double)v;
+            }
+        gr.sync();
+        for (int e = gr.rank; e < a.G * N; e += gr.size) PB[e] *= sc;
+        d2 = gr.sum(d2);
+        n2 = gr.sum(n2);
+        dphi = n2 > 0 ? sqrt(d2 / n2) : 0.0;
+        dk = fabs(kn - k) / fabs(kn);
+        k = kn;
+        if (dk <= a.tol_k && dphi <= a.tol) break;
+    }
+    if (status == NOP_OK && n > a.itmax) {
+        n = a.itmax;
+        status = NOP_ENOCONV;
+    }
+    if (gr.rank == 0) {
+        a.it_out[inst] = inner_total;
+        a.st_out[inst] = status;
+        a.ch_out[inst] = dphi;
+        a.k_out[inst] = k;
+        a.outer_out[inst] = n;
+    }
+    gr.sync();
+}
+
+template <typename T, bool BLOCK>
+__device__ __forceinline__ void dispatch(const Sn1dArgs& a, const Grp& gr, const Stage<T>& sg,
+                                         int inst) {
+    const int cfg = a.cfg[inst];
+    const int A = cfg & 0xff, lg = cfg >> 8;
+    switch (A) {
+        case 1: solve_instance<T, 1, BLOCK>(a, gr, sg, inst, lg); break;
+        case 2: solve_instance<T, 2, BLOCK>(a, gr, sg, inst, lg); break;
+        case 3: solve_instance<T, 3, BLOCK>(a, gr, sg, inst, lg); break;
+        case 4: solve_instance<T, 4, BLOCK>(a, gr, sg, inst, lg); break;
+        case 5: solve_instance<T, 5, BLOCK>(a, gr, sg, inst, lg); break;
+        case 6: solve_instance<T, 6, BLOCK>(a, gr, sg, inst, lg); break;
+        case 7: solve_instance<T, 7, BLOCK>(a, gr, sg, inst, lg); break;
+        default: solve_instance<T, 8, BLOCK>(a, gr, sg, inst, lg); break;
+    }
+}
+
+// Persistent kernel: blocks first drain the queue of large instances (the
+// whole block on one instance, its angles split over the warps), then every
+// warp drains the queue of small instances on its own.
+template <typename T>
+__global__ void __launch_bounds__(SN1D_THREADS) sn1d_kernel(Sn1dArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* smem = (T*)smem_raw;
+    __shared__ double red[SN1D_THREADS / 32];
+    __shared__ int job;
+    const int lane = threadIdx.x & 31;
+    Stage<T> sg;
+    sg.s = smem;
+    sg.pm = smem + a.smem_cells;
+    sg.pp = smem + 2 * a.smem_cells;
+    if (a.n_big > 0) {
+        Grp gb;
+        gb.block = true;
+        gb.rank = threadIdx.x;
+        gb.size = blockDim.x;
+        gb.warp = threadIdx.x >> 5;
+        gb.nwarps = blockDim.x >> 5;
+        gb.red = red;
+        for (;;) {
+            if (threadIdx.x == 0) job = atomicAdd(a.counter + 1, 1);
+            __syncthreads();
+            const int jb = job;
+            __syncthreads();
+            if (jb >= a.n_big) break;
+            dispatch<T, true>(a, gb, sg, a.big_list[jb]);
+        }
+    }
+    Grp gw;
+    gw.block = false;
+    gw.rank = lane;
+    gw.size = 32;
+    gw.warp = 0;
+    gw.nwarps = 1;
+    gw.red = nullptr;
+    for (;;) {
+        int jw = 0;
+        if (lane == 0) jw = atomicAdd(a.counter, 1);
+        jw = __shfl_sync(0xffffffffu, jw, 0);
+        if (jw >= a.n_small) return;
+        dispatch<T, false>(a, gw, sg, a.order_list[jw]);
+    }
+}
+
+// ---------------------------------------------------------------- set-up
+template <typename T>
+__global__ void sn1d_prepare(long long C, int G, const double* sigt, const double* sigs,
+                             const double* src, const double* nsf, const double* phi0,
+                             int phi0_flat, Cell4<T>* X, T* scat, T* ext, T* nsfT) {
+    const long long total = (long long)G * C;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int g = (int)(e / C);
+        const long long c = e - (long long)g * C;
+        Cell4<T> v;
+        v.st = (T)sigt[e];
+        v.y = (T)(0.5 * sigs[((long long)g * G + g) * C + c]);
+        const double ex = src ? 0.5 * src[e] : 0.0;
+        v.z = (T)ex;
+        v.phi = phi0 ? (T)phi0[e] : (phi0_flat ? T(1) : T(0));
+        X[e] = v;
+        ext[e] = (T)ex;
+        if (nsf) nsfT[e] = (T)nsf[e];
+        if (G > 1)
+            for (int gp = 0; gp < G; ++gp)
+                scat[((long long)gp * G + g) * C + c] = (T)(0.5 * sigs[((long long)gp * G + g) * C + c]);
+    }
+}
+
+template <typename T>
+__global__ void sn1d_finish(long long total, const Cell4<T>* X, double* phi) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x)
+        phi[e] = (double)X[e].phi;
+}
+
+template <typename T>
+int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* phi0,
+               const double* k0, double* phi_out, bool out_dev, double* k_out,
+               nop_stats* st) {
+    SlabDev& s = ctx->slab;
+    const int G = ctx->G;
+    const long long C = s.C;
+    const int B = s.n_inst;
+    void* p;
+    NOP_TRY(ctx->scratch("sn1d_X", sizeof(Cell4<T>) * G * C, &p));
+    Cell4<T>* X = (Cell4<T>*)p;
+    NOP_TRY(ctx->scratch("sn1d_U", sizeof(Cell2<T>) * G * C, &p));
+    Cell2<T>* U = (Cell2<T>*)p;
+    NOP_TRY(ctx->scratch("sn1d_scat", sizeof(T) * (G > 1 ? (long long)G * G * C : 1), &p));
+    T* scat = (T*)p;
+    NOP_TRY(ctx->scratch("sn1d_ext", sizeof(T) * G * C, &p));
+    T* ext = (T*)p;
+    NOP_TRY(ctx->scratch("sn1d_nsf", sizeof(T) * (eigen ? G * C : 1), &p));
+    T* nsf = (T*)p;
+    NOP_TRY(ctx->scratch("sn1d_phiprev", sizeof(T) * (eigen ? G * C : 1), &p));
+    T* phiprev = (T*)p;
+    NOP_TRY(ctx->scratch("sn1d_psib", sizeof(T) * std::max<long long>(1, s.bnd_total), &p));
+    T* psib = (T*)p;
+    NOP_TRY(ctx->scratch("sn1d_k0", sizeof(double) * B, &p));
+    double* k0_d = (double*)p;
+    NOP_TRY(ctx->scratch("sn1d_int", sizeof(int) * (5 * (size_t)B + 4), &p));
+    int* ints = (int*)p;
+    int* order_d = ints;
+    int* cfg_d = ints + B;
+    int* it_d = ints + 2 * B;
+    int* st_d = ints + 3 * B;
+    int* big_d = ints + 4 * B;
+    int* counter = ints + 5 * B;
+    NOP_TRY(ctx->scratch("sn1d_outer", sizeof(int) * B, &p));
+    int* outer_d = (int*)p;
+    NOP_TRY(ctx->scratch("sn1d_dbl", sizeof(double) * 2 * (size_t)B, &p));
+    double* ch_d = (double*)p;
+    double* kk_d = ch_d + B;
+
+    // ---- scheduling (host side).  Estimated work of an instance: cells x
+    // angles x iterations, the iterations from the largest in-group
+    // scattering ratio c (source iteration contracts roughly like c).  The
+    // persistent grid has `warps_total` warps; an instance worth more than
+    // twice a warp's fair share of the batch runs on a whole block (its angles
+    // split over the block's warps) so that it does not set the critical path.
+    const int blocks_max = ctx->sm_count * SN1D_BLOCKS_PER_SM;
+    const double tol_its = eigen ? std::min(o->tol_inner, o->tol) : o->tol;
+    std::vector<double> cost(B);
+    double total_cost = 0;
+    for (int b = 0; b < B; ++b) {
+        const double c = std::min(0.999, std::max(0.2, s.cmax[b]));
+        const double its = std::min(5000.0, std::max(5.0, std::log(tol_its) / std::log(c)));
+        cost[b] = (double)s.ncell[b] * s.order[b] * its * G;
+        total_cost += cost[b];
+    }
+    const int max_smem_cells = (int)(SN1D_SMEM_BYTES / (3 * sizeof(T)));
+    const int warps_total =
+        (int)std::max<long long>(1, std::min<long long>(B, (long long)blocks_max * (SN1D_THREADS / 32)));
+    const double share = total_cost / warps_total;
+    std::vector<int> cfg(B), small, big;
+    int smem_cells = 1;
+    for (int b = 0; b < B; ++b) {
+        const int h = s.order[b] / 2;
+        const bool is_big = B > 1 && cost[b] > 2.0 * share && h >= SN1D_THREADS / 32 &&
+                            s.ncell[b] <= max_smem_cells;
+        int lg, A;
+        if (is_big) {
+            const int hw = (h + SN1D_THREADS / 32 - 1) / (SN1D_THREADS / 32);
+            sn1d_pick_config(s.ncell[b], 2 * hw, &lg, &A);
+            big.push_back(b);
+            smem_cells = std::max(smem_cells, s.ncell[b]);
+        } else {
+            sn1d_pick_config(s.ncell[b], s.order[b], &lg, &A);
+            small.push_back(b);
+        }
+        cfg[b] = (lg << 8) | A;
+    }
+    auto longest_first = [&](int x, int y) { return cost[x] > cost[y]; };
+    std::stable_sort(small.begin(), small.end(), longest_first);
+    std::stable_sort(big.begin(), big.end(), longest_first);
+    std::vector<double> k0h(B, 1.0);
+    if (k0)
+        for (int b = 0; b < B; ++b) k0h[b] = k0[b] > 0 ? k0[b] : 1.0;
+    if (!small.empty())
+        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(order_d, small.data(), sizeof(int) * small.size(),
+                                          cudaMemcpyHostToDevice, ctx->stream));
+    if (!big.empty())
+        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(big_d, big.data(), sizeof(int) * big.size(),
+                                          cudaMemcpyHostToDevice, ctx->stream));
+    NOP_CUDA_TRY(ctx, cudaMemcpyAsync(cfg_d, cfg.data(), sizeof(int) * B,
+                                      cudaMemcpyHostToDevice, ctx->stream));
+    NOP_CUDA_TRY(ctx, cudaMemcpyAsync(k0_d, k0h.data(), sizeof(double) * B,
+                                      cudaMemcpyHostToDevice, ctx->stream));
+    NOP_CUDA_TRY(ctx, cudaMemsetAsync(counter, 0, 2 * sizeof(int), ctx->stream));
+
+    const long long total = (long long)G * C;
+    const int pblocks = (int)std::min<long long>((total + 255) / 256, 4LL * ctx->sm_count * 8);
+    int mk = ctx->phase_begin(2);
+    sn1d_prepare<T><<<std::max(1, pblocks), 256, 0, ctx->stream>>>(
+        C, G, ctx->sigt_d, ctx->sigs_d, eigen ? nullptr : ctx->src_d,
+        eigen ? ctx->nsf_d : nullptr, phi0, (eigen && !phi0) ? 1 : 0, X, scat, ext, nsf);
+    NOP_CUDA_TRY(ctx, cudaGetLastError());
+    ctx->phase_end(mk);
+    ctx->count_launch(false);
+
+    Sn1dArgs a;
+    a.n_inst = B;
+    a.G = G;
+    a.C = C;
+    a.order_list = order_d;
+    a.n_small = (int)small.size();
+    a.big_list = big_d;
+    a.n_big = (int)big.size();
+    a.smem_cells = smem_cells;
+    a.counter = counter;
+    a.cell_off = s.cell_off_d;
+    a.ncell = s.ncell_d;
+    a.nang = s.nang_d;
+    a.dx = s.dx_d;
+    a.qoff = s.qoff_d;
+    a.mu = s.mu_d;
+    a.w = s.w_d;
+    a.boff = s.boff_d;
+    a.cfg = cfg_d;
+    a.X = X;
+    a.U = U;
+    a.scat = scat;
+    a.ext = ext;
+    a.psib = psib;
+    a.bc_left = ctx->bc[0];
+    a.bc_right = ctx->bc[1];
+    a.eigen = eigen ? 1 : 0;
+    a.nsf = nsf;
+    a.chi = ctx->chi_d;
+    a.phiprev = phiprev;
+    a.k0 = k0_d;
+    a.tol = o->tol;
+    a.tol_inner = o->tol_inner;
+    a.tol_k = o->tol_k;
+    a.itmax = o->itmax;
+    a.itmax_inner = o->itmax_inner;
+    a.it_out = it_d;
+    a.st_out = st_d;
+    a.ch_out = ch_d;
+    a.k_out = kk_d;
+    a.outer_out = outer_d;
+    const int blocks = (int)std::max<long long>(
+        1, std::min<long long>(blocks_max, (long long)big.size() +
+                                               ((long long)small.size() + SN1D_THREADS / 32 - 1) /
+                                                   (SN1D_THREADS / 32)));
+    const size_t smem = 3 * sizeof(T) * (size_t)smem_cells;
+    NOP_CUDA_TRY(ctx, cudaFuncSetAttribute(sn1d_kernel<T>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)SN1D_SMEM_BYTES));
+    mk = ctx->phase_begin(0);
+    sn1d_kernel<T><<<blocks, SN1D_THREADS, smem, ctx->stream>>>(a);
+    NOP_CUDA_TRY(ctx, cudaGetLastError());
+    ctx->phase_end(mk);
+    ctx->count_launch(true);
+    if (phi_out) {
+        double* dst = phi_out;
+        if (!out_dev) {
+            NOP_TRY(ctx->scratch("sn1d_phiout", sizeof(double) * total, &p));
+            dst = (double*)p;
+        }
+        mk = ctx->phase_begin(2);
+        sn1d_finish<T><<<std::max(1, pblocks), 256, 0, ctx->stream>>>(total, X, dst);
+        NOP_CUDA_TRY(ctx, cudaGetLastError());
+        ctx->phase_end(mk);
+        ctx->count_launch(false);
+        if (!out_dev)
+            NOP_CUDA_TRY(ctx, cudaMemcpyAsync(phi_out, dst, sizeof(double) * total,
+                                              cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    if (eigen && k_out) {
+        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(k_out, kk_d, sizeof(double) * B,
+                                          out_dev ? cudaMemcpyDeviceToDevice
+                                                  : cudaMemcpyDeviceToHost,
+                                          ctx->stream));
+    }
+    if (out_dev && !st) {
+        // the host vectors above are read by the copies: wait for them
+        NOP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        return NOP_OK;
+    }
+    std::vector<int> it_h(B), st_h(B), out_h(B);
+    std::vector<double> ch_h(B);
+    NOP_CUDA_TRY(ctx, cudaMemcpyAsync(it_h.data(), it_d, sizeof(int) * B,
+                                      cudaMemcpyDeviceToHost, ctx->stream));
+    NOP_CUDA_TRY(ctx, cudaMemcpyAsync(st_h.data(), st_d, sizeof(int) * B,
+                                      cudaMemcpyDeviceToHost, ctx->stream));
+    NOP_CUDA_TRY(ctx, cudaMemcpyAsync(out_h.data(), outer_d, sizeof(int) * B,
+                                      cudaMemcpyDeviceToHost, ctx->stream));
+    NOP_CUDA_TRY(ctx, cudaMemcpyAsync(ch_h.data(), ch_d, sizeof(double) * B,
+                                      cudaMemcpyDeviceToHost, ctx->stream));
+    NOP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    int worst = NOP_OK;
+    if (st) {
+        st->max_iterations = 0;
+        st->sum_iterations = 0;
+        st->max_outer = 0;
+        st->max_change = 0;
+    }
+    for (int b = 0; b < B; ++b) {
+        if (ctx->timing)
+            ctx->cell_angle_updates += (double)it_h[b] * s.ncell[b] * s.order[b] * G;
+        if (st_h[b] != NOP_OK && (worst == NOP_OK || st_h[b] == NOP_ENAN)) worst = st_h[b];
+        if (st) {
+            st->max_iterations = std::max(st->max_iterations, it_h[b]);
+            st->sum_iterations += it_h[b];
+            if (eigen) st->max_outer = std::max(st->max_outer, out_h[b]);
+            st->max_change = std::max(st->max_change, ch_h[b]);
+            if (st->inst_iterations) st->inst_iterations[b] = it_h[b];
+            if (st->inst_status) st->inst_status[b] = st_h[b];
+        }
+    }
+    if (st) st->status = worst;
+    return worst;
+}
+
+}  // namespace nop

@@ -1,0 +1,227 @@
+"""GPU parity of the 1D slab solver (C ABI) against the FP64 oracle.
+
+Tolerances: FP64 sweeps agree with the oracle to rounding (1e-9 relative or
+tighter).  FP32 sweeps: scalar flux relative L2 <= 1e-5 and |dk| <= 1e-6
+against the oracle, the bar the workloads state.  Where both sides stop at
+the same relative-change tolerance they are compared iterate to iterate;
+where the GPU answer is compared with a fully converged oracle, the GPU runs
+to a tolerance tight enough that its truncation error is below the bar.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import quadrature as Qd
+from oracle import transport as T
+from tests.helpers import oracle_slab, rel_l2, slab_batch_arrays, split
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def solver():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2509_01416_gb300 import Solver
+    s = Solver(0)
+    yield s
+    s.close()
+
+
+def _set(s, insts, bc=(0, 0)):
+    n, wdt, order, sigt, sigs, src, nsf = slab_batch_arrays(insts)
+    s.set_slabs(n, wdt, order, sigt, sigs, source=src, nu_sigma_f=nsf,
+                chi=None if nsf is None else [1.0], bc=bc)
+
+
+def test_gauss_legendre_on_device_matches_oracle(solver):
+    orders = [2, 4, 8, 16, 32, 64, 128, 10, 26]
+    insts = [W.Slab1G(I=3, N=N, sigt=np.ones(3), sigs=np.zeros(3), Q=np.ones(3)) for N in orders]
+    _set(solver, insts)
+    for b, N in enumerate(orders):
+        mu, _, w = solver.quadrature(b)
+        m0, w0 = Qd.gauss_legendre(N)
+        assert np.max(np.abs(mu - m0)) < 1e-14 and np.max(np.abs(w - w0)) < 1e-14
+
+
+def test_config1_fp64_matches_oracle_iteration_for_iteration(solver):
+    c = W.config1()
+    _set(solver, [c])
+    phi, info = solver.solve_fixed_source(tol=1e-8, itmax=10000, precision=1)
+    r = T.source_iteration(oracle_slab(c), Qd.gauss_legendre(c.N), tol=1e-8)
+    assert abs(int(info["iterations"][0]) - r.iterations) <= 1
+    assert rel_l2(phi, r.phi[0]) < 1e-10
+    assert info["status"][0] == 0
+
+
+def test_config2_fp32_within_workload_tolerance(solver):
+    c = W.config2()
+    _set(solver, [c])
+    quad = Qd.gauss_legendre(c.N)
+    phi, info = solver.solve_fixed_source(tol=1e-6, itmax=20000, precision=0)
+    same_rule = T.source_iteration(oracle_slab(c), quad, tol=1e-6)
+    assert rel_l2(phi, same_rule.phi[0]) <= 1e-5
+    assert abs(int(info["iterations"][0]) - same_rule.iterations) <= 2
+    conv = T.source_iteration(oracle_slab(c), quad, tol=1e-13)
+    tight, info2 = solver.solve_fixed_source(tol=2e-7, itmax=40000, precision=0)
+    assert rel_l2(tight, conv.phi[0]) <= 1e-5, info2
+
+
+def test_config3_eigen_fp32(solver):
+    c = W.config3()
+    _set(solver, [c])
+    quad = Qd.gauss_legendre(c.N)
+    # same stopping rule on both sides (tol 1e-6 flux, 1e-7 in k, inner 1e-6)
+    k, phi, info = solver.solve_eigen(tol=1e-6, tol_k=1e-7, tol_inner=1e-6, itmax=2000,
+                                      precision=0)
+    same = T.power_iteration(oracle_slab(c), quad, tol_k=1e-7, tol_phi=1e-6, tol_inner=1e-6)
+    assert abs(k[0] - same.k) <= 1e-6, (k[0], same.k, info)
+    assert rel_l2(phi, same.phi[0]) <= 1e-5
+    # run to a tolerance whose truncation error is below the bar: converged oracle
+    e = T.power_iteration(oracle_slab(c), quad, tol_k=1e-12, tol_phi=1e-10, tol_inner=1e-12)
+    assert 0.85 < e.k < 1.15
+    k2, phi2, info2 = solver.solve_eigen(tol=1e-7, tol_k=1e-9, tol_inner=1e-7, itmax=5000,
+                                         itmax_inner=2000, precision=0, check=False)
+    assert abs(k2[0] - e.k) <= 1e-6, (k2[0], e.k, info2)
+    assert rel_l2(phi2, e.phi[0]) <= 1e-5
+
+
+def _table10():
+    S = np.array([[0.024, 0.171, 0.033], [0.0, 0.6, 0.275], [0.0, 0.0, 2.0]])
+    nu = np.array([3.0, 2.5, 2.0])
+    st = np.array([0.24, 0.975, 3.0])
+    sf = np.array([0.006, 0.06, 0.9])
+    chi = np.array([0.96, 0.04, 0.0])
+    return S, nu * sf, st, chi
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_table10_three_group_eigenvalue_on_gpu(solver, precision):
+    S, nsf, st, chi = _table10()
+    I = 100
+    solver.set_slabs([I], [10.0], [32], np.repeat(st, I), np.repeat(S.reshape(-1), I),
+                     nu_sigma_f=np.repeat(nsf, I), chi=chi)
+    P = T.Slab(dx=np.full(I, 0.1), sigt=st[:, None] * np.ones(I), sigs=S[:, :, None] * np.ones(I),
+               nusigf=nsf[:, None] * np.ones(I), chi=chi)
+    quad = Qd.gauss_legendre(32)
+    if precision == 1:
+        # FP64: same stopping rule, compared iterate to iterate
+        k, phi, info = solver.solve_eigen(tol=1e-7, tol_k=1e-9, tol_inner=1e-8, itmax=500,
+                                          precision=1)
+        e = T.power_iteration(P, quad, tol_k=1e-9, tol_phi=1e-7, tol_inner=1e-8)
+        assert abs(k[0] - e.k) <= 1e-10, (k[0], e.k)
+        assert rel_l2(phi, e.phi.reshape(-1)) <= 1e-9
+    else:
+        k, phi, info = solver.solve_eigen(tol=1e-7, tol_k=1e-9, tol_inner=1e-7, itmax=500,
+                                          itmax_inner=3000, precision=0, check=False)
+        e = T.power_iteration(P, quad, tol_k=1e-12, tol_phi=1e-10, tol_inner=1e-12)
+        assert abs(k[0] - e.k) <= 1e-6, (k[0], e.k, info)
+        assert rel_l2(phi, e.phi.reshape(-1)) <= 1e-5
+    # the paper's printed value (Table 10)
+    assert abs(k[0] - 1.30621) <= 5e-6, (k, info)
+
+
+@pytest.mark.parametrize("bc", [(1, 1), (1, 0), (0, 1)])
+def test_reflective_boundaries(solver, bc):
+    rng = np.random.default_rng(sum(bc) * 7 + bc[0])
+    I = 37
+    st = rng.uniform(0.5, 1.5, I)
+    inst = W.Slab1G(I=I, N=12, sigt=st, sigs=st * rng.uniform(0.3, 0.95, I),
+                    Q=rng.uniform(0, 1, I), L=6.0)
+    _set(solver, [inst], bc=bc)
+    phi, info = solver.solve_fixed_source(tol=1e-13, itmax=200000, precision=1)
+    r = T.source_iteration(oracle_slab(inst, bc), Qd.gauss_legendre(12), tol=1e-13,
+                           itmax=200000)
+    assert rel_l2(phi, r.phi[0]) < 1e-9
+    if bc == (1, 1):
+        flat = W.Slab1G(I=20, N=8, sigt=np.full(20, 1.3), sigs=np.full(20, 0.9), Q=np.full(20, 2.0))
+        _set(solver, [flat], bc=bc)
+        for prec, tol in ((1, 1e-10), (0, 1e-5)):
+            phi, _ = solver.solve_fixed_source(tol=1e-12 if prec else 1e-7, itmax=200000,
+                                               precision=prec, check=False)
+            assert np.max(np.abs(phi - 5.0)) / 5.0 < tol
+
+
+def test_ragged_batch_fp64_every_instance(solver):
+    rng = np.random.default_rng(21)
+    insts = []
+    for b in range(40):
+        I = int(rng.integers(1, 300)) if b > 1 else (1 if b == 0 else 2)
+        N = 2 * int(rng.integers(1, 17)) if b > 1 else 2
+        insts.append(W.slab_instance(np.random.default_rng(b), I, N))
+    _set(solver, insts)
+    phi, info = solver.solve_fixed_source(tol=1e-12, itmax=200000, precision=1)
+    for s, ph in zip(insts, split(phi, insts)):
+        r = T.source_iteration(oracle_slab(s), Qd.gauss_legendre(s.N), tol=1e-12, itmax=200000)
+        assert rel_l2(ph, r.phi[0]) < 1e-9, (s.I, s.N)
+    assert np.all(info["status"] == 0)
+
+
+def test_ragged_batch_fp32_same_rule(solver):
+    rng = np.random.default_rng(22)
+    insts = [W.slab_instance(np.random.default_rng(100 + b), int(rng.integers(20, 400)),
+                             2 * int(rng.integers(4, 33))) for b in range(64)]
+    _set(solver, insts)
+    phi, info = solver.solve_fixed_source(tol=1e-6, itmax=50000, precision=0)
+    for b, (s, ph) in enumerate(zip(insts, split(phi, insts))):
+        if b % 4:
+            continue
+        r = T.source_iteration(oracle_slab(s), Qd.gauss_legendre(s.N), tol=1e-6)
+        assert rel_l2(ph, r.phi[0]) <= 1e-5, (s.I, s.N)
+
+
+def test_full_batch_config5_sampled(solver):
+    insts = W.config5()
+    _set(solver, insts)
+    phi, info = solver.solve_fixed_source(tol=1e-6, itmax=50000, precision=0)
+    assert np.all(info["status"] == 0)
+    parts = split(phi, insts)
+    for b in np.random.default_rng(0).choice(len(insts), 6, replace=False):
+        s = insts[b]
+        r = T.source_iteration(oracle_slab(s), Qd.gauss_legendre(s.N), tol=1e-6)
+        assert rel_l2(parts[b], r.phi[0]) <= 1e-5, (b, s.I, s.N)
+        assert abs(int(info["iterations"][b]) - r.iterations) <= 2
+
+
+def test_multigroup_upscatter_fixed_source_fp64(solver):
+    rng = np.random.default_rng(11)
+    I, G = 30, 2
+    sigt = rng.uniform(0.8, 1.6, (G, I))
+    S = np.zeros((G, G, I))
+    S[0, 0], S[0, 1] = 0.3 * sigt[0], 0.3 * sigt[0]
+    S[1, 1], S[1, 0] = 0.5 * sigt[1], 0.2 * sigt[1]
+    Q = rng.uniform(0, 1, (G, I))
+    solver.set_slabs([I], [7.0], [8], sigt.reshape(-1), S.reshape(-1), source=Q.reshape(-1))
+    phi, info = solver.solve_fixed_source(tol=1e-13, itmax=100000, precision=1)
+    P = T.Slab(dx=np.full(I, 7.0 / I), sigt=sigt, sigs=S, Q=Q)
+    r = T.source_iteration(P, Qd.gauss_legendre(8), tol=1e-13)
+    assert rel_l2(phi, r.phi.reshape(-1)) < 1e-10
+
+
+def test_eigen_batch_of_different_shapes(solver):
+    insts = []
+    for b, (I, N) in enumerate([(40, 8), (75, 16), (120, 32), (9, 4)]):
+        st = np.full(I, 1.0 + 0.1 * b)
+        insts.append(W.Slab1G(I=I, N=N, sigt=st, sigs=0.5 * st, nusigf=np.full(I, 0.7 + 0.05 * b)))
+    _set(solver, insts)
+    k, phi, info = solver.solve_eigen(tol=1e-10, tol_k=1e-12, tol_inner=1e-12, itmax=5000,
+                                      precision=1)
+    for b, s in enumerate(insts):
+        e = T.power_iteration(oracle_slab(s), Qd.gauss_legendre(s.N), tol_k=1e-13,
+                              tol_phi=1e-11, tol_inner=1e-13)
+        assert abs(k[b] - e.k) < 1e-9
+
+
+def test_errors_and_caps(solver):
+    from paper_2509_01416_gb300 import NopError
+    with pytest.raises(NopError):
+        solver.set_slabs([5], [1.0], [3], np.ones(5), np.zeros(5), source=np.ones(5))
+    with pytest.raises(NopError):
+        solver.set_slabs([5], [1.0], [4], -np.ones(5), np.zeros(5), source=np.ones(5))
+    c = W.config1()
+    _set(solver, [c])
+    phi, info = solver.solve_fixed_source(tol=1e-12, itmax=3, precision=0, check=False)
+    assert info["rc"] == -4 and info["status"][0] == -4 and info["iterations"][0] == 3
+    with pytest.raises(NopError):
+        solver.solve_eigen(tol=1e-6)         # no production cross section
