@@ -277,6 +277,10 @@ def main():
                      "peak_source": "SFU reciprocal rate 16/clk/SM x %d SMs x %.0f MHz "
                                     "(sm_max_mhz, %s)" % (n_sm, smx, src_peak),
                      "sweep_ms_per_step": tm["sweep_ms"] / args.steps,
+                     "last_step_trace": {"span_ms": tm["last_span_ms"],
+                                         "longest_instance_ms": tm["last_inst_max_ms"],
+                                         "mean_instance_ms": tm["last_inst_mean_ms"],
+                                         "block_instances": tm["last_block_instances"]},
                      "sweep_algorithmic_gbs": sweep_gbs,
                      "sweep_algorithmic_frac_of_hbm": sweep_gbs / float(peaks.get("hbm_gbs", 6800.0))},
         "cpu_baseline": cpu,

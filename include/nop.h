@@ -68,6 +68,10 @@ extern "C" {
                               not synchronise (results valid once the context
                               stream reaches this point)                      */
 
+#define NOP_SCHED_AUTO   0
+#define NOP_SCHED_WARP   1
+#define NOP_SCHED_BLOCK  2
+
 typedef struct nop_ctx nop_ctx;
 
 /* Problem description, copied into device memory by nop_set_problem.
@@ -119,6 +123,9 @@ typedef struct {
     double recast_tol;     /* recast loop tolerance (Eq. 24)                   */
     int recast_itmax;      /* recast loop iteration cap                        */
     int flags;             /* NOP_PHI0_DEVICE | NOP_OUT_DEVICE                 */
+    int schedule;          /* slab batches: NOP_SCHED_AUTO, NOP_SCHED_WARP (one
+                              warp per instance), NOP_SCHED_BLOCK (a whole block
+                              per instance where the angles allow it)         */
 } nop_solve_opts;
 
 /* Per-call statistics (host struct).  Per-instance arrays are optional
@@ -213,6 +220,11 @@ typedef struct {
                                   instances of iterations x cells x angles x
                                   groups (one diamond-difference cell update per
                                   cell, direction and group)                     */
+    double last_span_ms;     /* last slab solve: first instance start to last
+                                instance end (device clock)                     */
+    double last_inst_max_ms; /* last slab solve: longest single instance         */
+    double last_inst_mean_ms;/* last slab solve: mean instance duration          */
+    int last_block_instances;/* last slab solve: instances run on a whole block  */
 } nop_timings;
 
 /* enable != 0: from now on record CUDA events around every kernel phase on

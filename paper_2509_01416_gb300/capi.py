@@ -19,6 +19,7 @@ NOP_BC_VACUUM, NOP_BC_REFLECTIVE = 0, 1
 NOP_PREC_F32, NOP_PREC_F64 = 0, 1
 NOP_WARM_NONE, NOP_WARM_RECAST = 0, 1
 NOP_PHI0_DEVICE, NOP_OUT_DEVICE = 1, 2
+NOP_SCHED_AUTO, NOP_SCHED_WARP, NOP_SCHED_BLOCK = 0, 1, 2
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
@@ -36,7 +37,7 @@ class nop_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("tol_k", C.c_double), ("tol_inner", C.c_double),
                 ("itmax", C.c_int), ("itmax_inner", C.c_int), ("precision", C.c_int),
                 ("warm_start", C.c_int), ("recast_tol", C.c_double),
-                ("recast_itmax", C.c_int), ("flags", C.c_int)]
+                ("recast_itmax", C.c_int), ("flags", C.c_int), ("schedule", C.c_int)]
 
 
 class nop_stats(C.Structure):
@@ -50,7 +51,9 @@ class nop_stats(C.Structure):
 class nop_timings(C.Structure):
     _fields_ = [("sweep_ms", C.c_double), ("operator_ms", C.c_double),
                 ("setup_ms", C.c_double), ("launches", C.c_longlong),
-                ("sweep_launches", C.c_longlong), ("cell_angle_updates", C.c_double)]
+                ("sweep_launches", C.c_longlong), ("cell_angle_updates", C.c_double),
+                ("last_span_ms", C.c_double), ("last_inst_max_ms", C.c_double),
+                ("last_inst_mean_ms", C.c_double), ("last_block_instances", C.c_int)]
 
 
 # every symbol include/nop.h declares, with its ctypes signature

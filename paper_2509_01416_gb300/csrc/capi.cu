@@ -170,6 +170,10 @@ int nop_get_timing(nop_ctx* ctx, nop_timings* out) {
     out->launches = ctx->launches;
     out->sweep_launches = ctx->sweep_launches;
     out->cell_angle_updates = ctx->cell_angle_updates;
+    out->last_span_ms = ctx->trace_span_ms;
+    out->last_inst_max_ms = ctx->trace_max_ms;
+    out->last_inst_mean_ms = ctx->trace_mean_ms;
+    out->last_block_instances = ctx->trace_big;
     return NOP_OK;
 }
 

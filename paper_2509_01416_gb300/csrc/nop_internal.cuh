@@ -92,6 +92,9 @@ struct nop_ctx {
     std::vector<cudaEvent_t> event_pool;
     long long launches = 0, sweep_launches = 0;
     double cell_angle_updates = 0;
+    // per-instance trace summary of the last slab solve (timing on)
+    double trace_span_ms = 0, trace_max_ms = 0, trace_mean_ms = 0;
+    int trace_big = 0;
     // Open a timed phase on the stream; returns the mark index or -1.
     int phase_begin(int phase);
     void phase_end(int mark);
@@ -120,6 +123,6 @@ int sn1d_solve(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* 
                bool phi0_dev, const double* k0, double* phi_out, bool out_dev,
                double* k_out, nop_stats* st);
 
-// Autotuner for the 1D sweep: lanes per angle group (log2) and angles per lane.
+// Lane split of the 1D sweep (log2 lanes per angle group, angles per lane).
 void sn1d_pick_config(int cells, int order, int* lg_ng, int* A);
 }  // namespace nop

@@ -1,5 +1,5 @@
 // Dispatch of the batched 1D slab solver (kernels in sn1d_impl.cuh, compiled
-// once per precision in sn1d_f32.cu / sn1d_f64.cu) and its lane-split model.
+// once per precision in sn1d_f32.cu / sn1d_f64.cu).
 #include <algorithm>
 #include <cmath>
 
@@ -15,22 +15,28 @@ extern template int sn1d_run<float>(nop_ctx*, const nop_solve_opts*, bool, const
 extern template int sn1d_run<double>(nop_ctx*, const nop_solve_opts*, bool, const double*,
                                      const double*, double*, bool, double*, nop_stats*);
 
-// Cost model of one sweep of I cells with N angles for a lane split: a warp
-// instruction of the reciprocal takes 8 cycles of the SM sub-partition's
-// special-function unit, so a cell step costs max(8 A, issue slots); chunked
-// splits add the map-composition pass.
+// Lane-split model for one sweep of I cells with N angles: issue slots per
+// cell step of a warp (per-cell loads and ownership ~12, the xor reduction 2
+// per level, ~13 FP32 pipe instructions per angle in the compensated update),
+// bounded below by the reciprocal unit (8 cycles per warp instruction).
+// Chunked splits add the map-composition pass and a scan.  A lane carries
+// A in {1, 2, 4} angles (the compiled variants; wider lanes would raise the
+// kernel's register count and cut its occupancy).
 void sn1d_pick_config(int I, int N, int* lg_out, int* A_out) {
     const int h = N / 2;
     double best = 1e300;
-    int bl = 5, bA = (h + 31) / 32;
+    int bl = 5, bA = 4;
     for (int lg = 0; lg <= 5; ++lg) {
         const int ng = 1 << lg, nt = 32 >> lg;
-        const int A = (h + ng - 1) / ng;
-        if (A > 8) continue;
-        const int m = (I + nt - 1) / nt;
-        const double passB = std::max(8.0 * A, 6.0 * A + 2.0 * lg + 8.0);
-        const double passA = nt > 1 ? std::max(8.0 * A, 6.0 * A + 4.0) : 0.0;
-        const double scan = nt > 1 ? 4.0 * A * std::log2((double)nt) * 4.0 : 0.0;
+        const int need = (h + ng - 1) / ng;
+        int A = 1;
+        while (A < need) A <<= 1;
+        if (A > 4) continue;
+        const double m = (double)((I + nt - 1) / nt);
+        const double mufu = 8.0 * A;
+        const double passB = std::max(mufu, 12.0 + 2.0 * lg + 13.0 * A);
+        const double passA = nt > 1 ? std::max(mufu, 8.0 + 12.0 * A) : 0.0;
+        const double scan = nt > 1 ? 20.0 * A * std::log2((double)nt) : 0.0;
         const double cost = m * (passB + passA) + scan;
         if (cost < best) {
             best = cost;

@@ -28,8 +28,8 @@
 #include "nop_internal.cuh"
 
 #define SN1D_THREADS 256
-#define SN1D_BLOCKS_PER_SM 4
-#define SN1D_SMEM_BYTES (48 * 1024)
+#define SN1D_BLOCKS_PER_SM 3
+#define SN1D_SMEM_BYTES (72 * 1024)
 
 namespace nop {
 
@@ -39,7 +39,7 @@ struct alignas(4 * sizeof(T)) Cell4 {
 };
 template <typename T>
 struct alignas(2 * sizeof(T)) Cell2 {
-    T s, pm;
+    T s0, s1;
 };
 
 struct Sn1dArgs {
@@ -59,9 +59,9 @@ struct Sn1dArgs {
     const double* mu;
     const double* w;
     const long long* boff;
-    const int* cfg;
     void* X;
-    void* U;
+    void* U;              // Cell2 [C]: per-cell {s, phi_minus} of the warp path
+    const int* cfg;       // per instance: (log2 ng) << 8 | A
     const void* scat;     // T [G][G][C], halved; only read when G > 1
     void* ext;            // T [G][C], halved external / fission source
     void* psib;           // T boundary fluxes [boff + (g*h + hi)*2 + side]
@@ -81,6 +81,7 @@ struct Sn1dArgs {
     double* ch_out;
     double* k_out;
     int* outer_out;
+    unsigned long long* trace;   // optional [n_inst][3]: start ns, end ns, SM id
 };
 
 // Reciprocal for the DD cell solve.  FP32: the special-function unit's
@@ -122,22 +123,56 @@ struct Grp {
     }
 };
 
-// Shared-memory staging of the block path: source, and the two half-range
-// angle sums of every cell.
+// Shared-memory staging of the block path: the source of every cell and one
+// row of partial angle sums per warp (each warp owns its row, so the sweeps
+// need no atomics; the rows are added after the sweep).
 template <typename T>
 struct Stage {
     T* s;
-    T* pm;
-    T* pp;
+    T* part;      // [nwarps][cells]
+    int cells;
+};
+
+// Running sum carried along a sweep.  FP32 keeps a compensation term
+// (Fast2Sum: the rounding error of every add is fed into the next one), so the
+// angular flux carried across hundreds of optically thin cells does not
+// accumulate one rounding per cell; FP64 adds plainly.
+template <typename T>
+struct CSum {
+    T hi, lo;
+    __device__ __forceinline__ void set(T v) {
+        hi = v;
+        lo = T(0);
+    }
+    __device__ __forceinline__ void add(T d) {
+        if constexpr (sizeof(T) == 4) {
+            const T u = d + lo;
+            const T t = hi + u;
+            lo = u - (t - hi);
+            hi = t;
+        } else {
+            hi += d;
+        }
+    }
+    __device__ __forceinline__ T val() const { return hi + lo; }
 };
 
 // One direction half (MINUS: mu < 0, cells right to left) of one group, for
-// the angles this warp carries.  Warp path: the owner lane stores the MINUS
-// partial sum in U and completes the cell in the PLUS half.  Block path: the
-// source comes from shared memory and owners add their partial sums there.
-template <typename T, int A, bool MINUS, bool BLOCK>
-__device__ __forceinline__ void sweep_half(Cell4<T>* X, Cell2<T>* U, const Stage<T>& sg, int I,
-                                           int lg, const T (&cc)[A], const T (&wt)[A],
+// the angles this warp carries.  Lanes: nt = 32/ng cell chunks x ng angle
+// groups, A angles per lane.  Diamond difference in increment form: with
+// delta = (s - st psi_in) / (c + st), c = 2|mu|/dx,
+//     psi_cell = psi_in + delta,   psi_out = psi_in + 2 delta.
+// Chunked splits first compose each chunk's affine map psi_out = (1 - D)
+// psi_in + B (D = 1 - prod alpha kept as a deficit, B compensated), scan the
+// maps over the chunks, then sweep.  The angle sum of a cell is reduced over
+// the ng lanes of its chunk with xor shuffles; lane (k mod ng) owns the k-th
+// cell of the chunk.  Warp path: the owner stores the MINUS partial sum in U
+// and completes the cell in the PLUS half.  Block path: the source comes from
+// shared memory and owners add their partial sums there.
+template <typename T, int A, bool MINUS>
+__device__ __forceinline__ void sweep_half(const bool block, Cell4<T>* X, Cell2<T>* U,
+                                           const Stage<T>& sg, int I, int lg,
+                                           const T (&cc)[A], const T (&wt)[A],
                                            const T (&psi_bnd)[A], T (&psi_out)[A],
                                            double& acc_d, double& acc_n) {
     const int lane = threadIdx.x & 31;
@@ -146,56 +181,62 @@ __device__ __forceinline__ void sweep_half(Cell4<T>* X, Cell2<T>* U, const Stage
     const int m = (I + nt - 1) / nt;
     const int k0 = t * m;
     const int len = max(0, min(m, I - k0));
-    T psi[A];
+    CSum<T> psi[A];
 #pragma unroll
-    for (int q = 0; q < A; ++q) psi[q] = psi_bnd[q];
+    for (int q = 0; q < A; ++q) psi[q].set(psi_bnd[q]);
     if (nt > 1) {
-        T Ac[A], Bc[A];
+        CSum<T> Bc[A];
+        T D[A];
 #pragma unroll
         for (int q = 0; q < A; ++q) {
-            Ac[q] = T(1);
-            Bc[q] = T(0);
+            Bc[q].set(T(0));
+            D[q] = T(0);
         }
         for (int k = 0; k < len; ++k) {
             const int i = MINUS ? (I - 1 - (k0 + k)) : (k0 + k);
             T st, s;
-            if (BLOCK) {
+            if (block) {
                 st = X[i].st;
                 s = sg.s[i];
             } else {
                 const Cell4<T> v = X[i];
                 st = v.st;
-                s = MINUS ? (v.y * v.phi + v.z) : U[i].s;
+                s = MINUS ? (v.y * v.phi + v.z) : U[i].s0;
             }
 #pragma unroll
             for (int q = 0; q < A; ++q) {
-                const T r = rcp_dd(cc[q] + st);
-                const T al = (cc[q] - st) * r;
-                Bc[q] = al * Bc[q] + T(2) * s * r;
-                Ac[q] = al * Ac[q];
+                const T r2 = T(2) * rcp_dd(cc[q] + st);
+                D[q] = (r2 * st) * (T(1) - D[q]) + D[q];
+                Bc[q].add(r2 * (s - st * Bc[q].hi));
             }
         }
         // inclusive scan of the chunk maps along the sweep (lanes stride ng)
+        T Dv[A], Bv[A];
+#pragma unroll
+        for (int q = 0; q < A; ++q) {
+            Dv[q] = D[q];
+            Bv[q] = Bc[q].val();
+        }
         for (int d = 1; d < nt; d <<= 1) {
 #pragma unroll
             for (int q = 0; q < A; ++q) {
-                const T Ao = __shfl_up_sync(0xffffffffu, Ac[q], d << lg);
-                const T Bo = __shfl_up_sync(0xffffffffu, Bc[q], d << lg);
+                const T Do = __shfl_up_sync(0xffffffffu, Dv[q], d << lg);
+                const T Bo = __shfl_up_sync(0xffffffffu, Bv[q], d << lg);
                 if (t >= d) {
-                    Bc[q] = Ac[q] * Bo + Bc[q];
-                    Ac[q] = Ac[q] * Ao;
+                    Bv[q] = (Bo + Bv[q]) - Dv[q] * Bo;
+                    Dv[q] = Dv[q] * (T(1) - Do) + Do;
                 }
             }
         }
 #pragma unroll
         for (int q = 0; q < A; ++q) {
-            T Ae = __shfl_up_sync(0xffffffffu, Ac[q], ng);
-            T Be = __shfl_up_sync(0xffffffffu, Bc[q], ng);
+            T De = __shfl_up_sync(0xffffffffu, Dv[q], ng);
+            T Be = __shfl_up_sync(0xffffffffu, Bv[q], ng);
             if (t == 0) {
-                Ae = T(1);
+                De = T(0);
                 Be = T(0);
             }
-            psi[q] = Ae * psi_bnd[q] + Be;
+            psi[q].set((psi_bnd[q] + Be) - De * psi_bnd[q]);
         }
     }
 #pragma unroll 2
@@ -205,34 +246,33 @@ __device__ __forceinline__ void sweep_half(Cell4<T>* X, Cell2<T>* U, const Stage
         T p = T(0), s = T(0), phio = T(0);
         if (valid) {
             T st;
-            if (BLOCK) {
+            if (block) {
                 st = X[i].st;
                 s = sg.s[i];
             } else {
                 const Cell4<T> v = X[i];
                 st = v.st;
                 phio = v.phi;
-                s = MINUS ? (v.y * v.phi + v.z) : U[i].s;
+                s = MINUS ? (v.y * v.phi + v.z) : U[i].s0;
             }
 #pragma unroll
             for (int q = 0; q < A; ++q) {
-                const T r = rcp_dd(cc[q] + st);
-                const T pc = (s + cc[q] * psi[q]) * r;
-                psi[q] = T(2) * pc - psi[q];
-                p += wt[q] * pc;
+                const T dl = rcp_dd(cc[q] + st) * (s - st * psi[q].hi);
+                p += wt[q] * (psi[q].hi + (dl + psi[q].lo));
+                psi[q].add(dl + dl);
             }
         }
         for (int o = 1; o < ng; o <<= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
         if (valid && (k & (ng - 1)) == j) {
-            if (BLOCK) {
-                atomicAdd(MINUS ? &sg.pm[i] : &sg.pp[i], p);
+            if (block) {
+                sg.part[(threadIdx.x >> 5) * sg.cells + i] += p;
             } else if (MINUS) {
                 Cell2<T> u;
-                u.s = s;
-                u.pm = p;
+                u.s0 = s;
+                u.s1 = p;
                 U[i] = u;
             } else {
-                const T phin = p + U[i].pm;
+                const T phin = p + U[i].s1;
                 const double df = (double)phin - (double)phio;
                 acc_d += df * df;
                 acc_n += (double)phin * (double)phin;
@@ -242,7 +282,7 @@ __device__ __forceinline__ void sweep_half(Cell4<T>* X, Cell2<T>* U, const Stage
     }
 #pragma unroll
     for (int q = 0; q < A; ++q)
-        psi_out[q] = __shfl_sync(0xffffffffu, psi[q], ((nt - 1) << lg) + j);
+        psi_out[q] = __shfl_sync(0xffffffffu, psi[q].val(), ((nt - 1) << lg) + j);
 }
 
 // Out-of-group source of group g: z = ext/2 + sum_{g' != g} ss(g'->g)/2 phi_g'.
@@ -261,9 +301,9 @@ __device__ void group_source(const Sn1dArgs& a, const Grp& gr, long long off, in
 }
 
 // One source iteration over all groups; returns the relative L2 change.
-// `hb`/`hw`: this warp's slice of the half-angle range (the whole range on
-// the warp path).
-template <typename T, int A, bool BLOCK>
+// [hb, he): this warp's slice of the half-angle range (all of it on the warp
+// path).
+template <typename T, int A>
 __device__ double si_iteration(const Sn1dArgs& a, const Grp& gr, const Stage<T>& sg, int inst,
                                long long off, int I, int h, int hb, int he, int lg,
                                const T (&cc)[A], const T (&wt)[A]) {
@@ -277,13 +317,12 @@ __device__ double si_iteration(const Sn1dArgs& a, const Grp& gr, const Stage<T>&
             gr.sync();
         }
         Cell4<T>* X = (Cell4<T>*)a.X + (long long)g * a.C + off;
-        Cell2<T>* U = (Cell2<T>*)a.U + (long long)g * a.C + off;
-        if (BLOCK) {
+        Cell2<T>* U = (Cell2<T>*)a.U + off;
+        if (gr.block) {
             for (int i = gr.rank; i < I; i += gr.size) {
                 const Cell4<T> v = X[i];
                 sg.s[i] = v.y * v.phi + v.z;
-                sg.pm[i] = T(0);
-                sg.pp[i] = T(0);
+                for (int w = 0; w < gr.nwarps; ++w) sg.part[w * sg.cells + i] = T(0);
             }
             gr.sync();
         }
@@ -294,7 +333,7 @@ __device__ double si_iteration(const Sn1dArgs& a, const Grp& gr, const Stage<T>&
             const int hi = hb + j * A + q;
             bnd[q] = (a.bc_right && hi < he) ? PB[(g * h + hi) * 2 + 1] : T(0);
         }
-        sweep_half<T, A, true, BLOCK>(X, U, sg, I, lg, cc, wt, bnd, out, acc_d, acc_n);
+        sweep_half<T, A, true>(gr.block, X, U, sg, I, lg, cc, wt, bnd, out, acc_d, acc_n);
         __syncwarp();
 #pragma unroll
         for (int q = 0; q < A; ++q) {
@@ -302,16 +341,17 @@ __device__ double si_iteration(const Sn1dArgs& a, const Grp& gr, const Stage<T>&
             if (hi < he && (lane >> lg) == 0) PB[(g * h + hi) * 2 + 0] = out[q];
             bnd[q] = a.bc_left ? out[q] : T(0);
         }
-        sweep_half<T, A, false, BLOCK>(X, U, sg, I, lg, cc, wt, bnd, out, acc_d, acc_n);
+        sweep_half<T, A, false>(gr.block, X, U, sg, I, lg, cc, wt, bnd, out, acc_d, acc_n);
 #pragma unroll
         for (int q = 0; q < A; ++q) {
             const int hi = hb + j * A + q;
             if (hi < he && (lane >> lg) == 0) PB[(g * h + hi) * 2 + 1] = out[q];
         }
         gr.sync();
-        if (BLOCK) {
+        if (gr.block) {
             for (int i = gr.rank; i < I; i += gr.size) {
-                const T phin = sg.pm[i] + sg.pp[i];
+                T phin = T(0);
+                for (int w = 0; w < gr.nwarps; ++w) phin += sg.part[w * sg.cells + i];
                 const double df = (double)phin - (double)X[i].phi;
                 acc_d += df * df;
                 acc_n += (double)phin * (double)phin;
@@ -339,22 +379,23 @@ __device__ double production(const Sn1dArgs& a, const Grp& gr, long long off, in
     return gr.sum(acc) * dx;
 }
 
-template <typename T, int A, bool BLOCK>
+template <typename T, int A>
 __device__ void solve_instance(const Sn1dArgs& a, const Grp& gr, const Stage<T>& sg, int inst,
                                int lg) {
     const int lane = threadIdx.x & 31;
-    const int ng = 1 << lg;
-    const int j = lane & (ng - 1);
+    const int j = lane & ((1 << lg) - 1);
     const int I = a.ncell[inst];
     const int N = a.nang[inst];
     const int h = N / 2;
-    // this warp's slice of the half-angle range
-    const int hw = BLOCK ? (h + gr.nwarps - 1) / gr.nwarps : h;
-    const int hb = BLOCK ? min(h, gr.warp * hw) : 0;
-    const int he = BLOCK ? min(h, hb + hw) : h;
     const double dxv = a.dx[inst];
     const long long off = a.cell_off[inst];
     const int q0 = a.qoff[inst];
+    // this warp's slice of the half-angle range
+    const int hw = gr.block ? (h + gr.nwarps - 1) / gr.nwarps : h;
+    const int hb = gr.block ? min(h, gr.warp * hw) : 0;
+    const int he = gr.block ? min(h, hb + hw) : h;
+    unsigned long long t_start = 0;
+    if (a.trace && gr.rank == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
     T cc[A], wt[A];
 #pragma unroll
     for (int q = 0; q < A; ++q) {
@@ -373,127 +414,127 @@ __device__ void solve_instance(const Sn1dArgs& a, const Grp& gr, const Stage<T>&
 
     int status = NOP_OK;
     double change = 0.0;
+    int its = 0, n = 0;
+    double k = 0.0, dphi = INFINITY;
     if (!a.eigen) {
-        int it = 0;
-        for (it = 1; it <= a.itmax; ++it) {
-            change = si_iteration<T, A, BLOCK>(a, gr, sg, inst, off, I, h, hb, he, lg, cc, wt);
+        for (its = 1; its <= a.itmax; ++its) {
+            change = si_iteration<T, A>(a, gr, sg, inst, off, I, h, hb, he, lg, cc, wt);
             if (!isfinite(change)) {
                 status = NOP_ENAN;
                 break;
             }
             if (change <= a.tol) break;
         }
-        if (it > a.itmax) {
-            it = a.itmax;
+        if (its > a.itmax) {
+            its = a.itmax;
             status = NOP_ENOCONV;
         }
-        if (gr.rank == 0) {
-            a.it_out[inst] = it;
-            a.st_out[inst] = status;
-            a.ch_out[inst] = change;
+        dphi = change;
+    } else {
+        // ---- power iteration (App. A2): flux normalised to unit production
+        Cell4<T>* X = (Cell4<T>*)a.X;
+        T* PP = (T*)a.phiprev;
+        const T* F = (const T*)a.nsf;
+        T* E = (T*)a.ext;
+        k = a.k0[inst];
+        double P = production<T>(a, gr, off, I, dxv);
+        if (!(P > 0.0) || !isfinite(P)) status = NOP_ENAN;
+        if (status == NOP_OK) {
+            const T sc = (T)(1.0 / P);
+            for (int g = 0; g < a.G; ++g)
+                for (int i = gr.rank; i < I; i += gr.size) X[(long long)g * a.C + off + i].phi *= sc;
         }
         gr.sync();
-        return;
-    }
-
-    // ---- power iteration (App. A2): flux normalised to unit production
-    Cell4<T>* X = (Cell4<T>*)a.X;
-    T* PP = (T*)a.phiprev;
-    const T* F = (const T*)a.nsf;
-    T* E = (T*)a.ext;
-    double k = a.k0[inst];
-    double P = production<T>(a, gr, off, I, dxv);
-    if (!(P > 0.0) || !isfinite(P)) status = NOP_ENAN;
-    if (status == NOP_OK) {
-        const T sc = (T)(1.0 / P);
-        for (int g = 0; g < a.G; ++g)
-            for (int i = gr.rank; i < I; i += gr.size) X[(long long)g * a.C + off + i].phi *= sc;
-    }
-    gr.sync();
-    int inner_total = 0, n = 0;
-    double dk = INFINITY, dphi = INFINITY;
-    for (n = 1; n <= a.itmax && status == NOP_OK; ++n) {
-        // frozen fission source chi_g F / k (halved) and the previous flux
-        for (int i = gr.rank; i < I; i += gr.size) {
-            double Fi = 0.0;
-            for (int g = 0; g < a.G; ++g) {
-                const long long c = (long long)g * a.C + off + i;
-                Fi += (double)F[c] * (double)X[c].phi;
-                PP[c] = X[c].phi;
+        double dk = INFINITY;
+        for (n = 1; n <= a.itmax && status == NOP_OK; ++n) {
+            // frozen fission source chi_g F / k (halved) and the previous flux
+            for (int i = gr.rank; i < I; i += gr.size) {
+                double Fi = 0.0;
+                for (int g = 0; g < a.G; ++g) {
+                    const long long c = (long long)g * a.C + off + i;
+                    Fi += (double)F[c] * (double)X[c].phi;
+                    PP[c] = X[c].phi;
+                }
+                for (int g = 0; g < a.G; ++g) {
+                    const long long c = (long long)g * a.C + off + i;
+                    const T e = (T)(0.5 * a.chi[g] * Fi / k);
+                    E[c] = e;
+                    if (a.G == 1) X[c].z = e;
+                }
             }
-            for (int g = 0; g < a.G; ++g) {
-                const long long c = (long long)g * a.C + off + i;
-                const T e = (T)(0.5 * a.chi[g] * Fi / k);
-                E[c] = e;
-                if (a.G == 1) X[c].z = e;
+            gr.sync();
+            int it;
+            for (it = 1; it <= a.itmax_inner; ++it) {
+                change = si_iteration<T, A>(a, gr, sg, inst, off, I, h, hb, he, lg, cc, wt);
+                if (!isfinite(change)) {
+                    status = NOP_ENAN;
+                    break;
+                }
+                if (change <= a.tol_inner) break;
             }
-        }
-        gr.sync();
-        int it;
-        for (it = 1; it <= a.itmax_inner; ++it) {
-            change = si_iteration<T, A, BLOCK>(a, gr, sg, inst, off, I, h, hb, he, lg, cc, wt);
-            if (!isfinite(change)) {
+            its += min(it, a.itmax_inner);
+            if (status != NOP_OK) break;
+            P = production<T>(a, gr, off, I, dxv);
+            if (!(P > 0.0) || !isfinite(P)) {
                 status = NOP_ENAN;
                 break;
             }
-            if (change <= a.tol_inner) break;
+            const double kn = k * P;
+            const T sc = (T)(1.0 / P);
+            double d2 = 0.0, n2 = 0.0;
+            for (int g = 0; g < a.G; ++g)
+                for (int i = gr.rank; i < I; i += gr.size) {
+                    const long long c = (long long)g * a.C + off + i;
+                    const T v = X[c].phi * sc;
+                    X[c].phi = v;
+                    const double df = (double)v - (double)PP[c];
+                    d2 += df * df;
+                    n2 += (double)v * (double)v;
+                }
+            gr.sync();
+            for (int e = gr.rank; e < a.G * N; e += gr.size) PB[e] *= sc;
+            d2 = gr.sum(d2);
+            n2 = gr.sum(n2);
+            dphi = n2 > 0 ? sqrt(d2 / n2) : 0.0;
+            dk = fabs(kn - k) / fabs(kn);
+            k = kn;
+            if (dk <= a.tol_k && dphi <= a.tol) break;
         }
-        inner_total += min(it, a.itmax_inner);
-        if (status != NOP_OK) break;
-        P = production<T>(a, gr, off, I, dxv);
-        if (!(P > 0.0) || !isfinite(P)) {
-            status = NOP_ENAN;
-            break;
+        if (status == NOP_OK && n > a.itmax) {
+            n = a.itmax;
+            status = NOP_ENOCONV;
         }
-        const double kn = k * P;
-        const T sc = (T)(1.0 / P);
-        double d2 = 0.0, n2 = 0.0;
-        for (int g = 0; g < a.G; ++g)
-            for (int i = gr.rank; i < I; i += gr.size) {
-                const long long c = (long long)g * a.C + off + i;
-                const T v = X[c].phi * sc;
-                X[c].phi = v;
-                const double df = (double)v - (double)PP[c];
-                d2 += df * df;
-                n2 += (double)v * (double)v;
-            }
-        gr.sync();
-        for (int e = gr.rank; e < a.G * N; e += gr.size) PB[e] *= sc;
-        d2 = gr.sum(d2);
-        n2 = gr.sum(n2);
-        dphi = n2 > 0 ? sqrt(d2 / n2) : 0.0;
-        dk = fabs(kn - k) / fabs(kn);
-        k = kn;
-        if (dk <= a.tol_k && dphi <= a.tol) break;
-    }
-    if (status == NOP_OK && n > a.itmax) {
-        n = a.itmax;
-        status = NOP_ENOCONV;
     }
     if (gr.rank == 0) {
-        a.it_out[inst] = inner_total;
+        a.it_out[inst] = its;
         a.st_out[inst] = status;
         a.ch_out[inst] = dphi;
-        a.k_out[inst] = k;
-        a.outer_out[inst] = n;
+        if (a.eigen) {
+            a.k_out[inst] = k;
+            a.outer_out[inst] = n;
+        }
+        if (a.trace) {
+            unsigned long long t_end;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
+            unsigned int smid;
+            asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+            a.trace[3 * (long long)inst + 0] = t_start;
+            a.trace[3 * (long long)inst + 1] = t_end;
+            a.trace[3 * (long long)inst + 2] = smid | (gr.block ? 0x80000000ull : 0ull);
+        }
     }
     gr.sync();
 }
 
-template <typename T, bool BLOCK>
+template <typename T>
 __device__ __forceinline__ void dispatch(const Sn1dArgs& a, const Grp& gr, const Stage<T>& sg,
                                          int inst) {
     const int cfg = a.cfg[inst];
     const int A = cfg & 0xff, lg = cfg >> 8;
     switch (A) {
-        case 1: solve_instance<T, 1, BLOCK>(a, gr, sg, inst, lg); break;
-        case 2: solve_instance<T, 2, BLOCK>(a, gr, sg, inst, lg); break;
-        case 3: solve_instance<T, 3, BLOCK>(a, gr, sg, inst, lg); break;
-        case 4: solve_instance<T, 4, BLOCK>(a, gr, sg, inst, lg); break;
-        case 5: solve_instance<T, 5, BLOCK>(a, gr, sg, inst, lg); break;
-        case 6: solve_instance<T, 6, BLOCK>(a, gr, sg, inst, lg); break;
-        case 7: solve_instance<T, 7, BLOCK>(a, gr, sg, inst, lg); break;
-        default: solve_instance<T, 8, BLOCK>(a, gr, sg, inst, lg); break;
+        case 1: solve_instance<T, 1>(a, gr, sg, inst, lg); break;
+        case 2: solve_instance<T, 2>(a, gr, sg, inst, lg); break;
+        default: solve_instance<T, 4>(a, gr, sg, inst, lg); break;
     }
 }
 
@@ -501,16 +542,16 @@ __device__ __forceinline__ void dispatch(const Sn1dArgs& a, const Grp& gr, const
 // whole block on one instance, its angles split over the warps), then every
 // warp drains the queue of small instances on its own.
 template <typename T>
-__global__ void __launch_bounds__(SN1D_THREADS) sn1d_kernel(Sn1dArgs a) {
+__global__ void __launch_bounds__(SN1D_THREADS, SN1D_BLOCKS_PER_SM) sn1d_kernel(Sn1dArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* smem = (T*)smem_raw;
     __shared__ double red[SN1D_THREADS / 32];
     __shared__ int job;
     const int lane = threadIdx.x & 31;
+    T* smem = (T*)smem_raw;
     Stage<T> sg;
     sg.s = smem;
-    sg.pm = smem + a.smem_cells;
-    sg.pp = smem + 2 * a.smem_cells;
+    sg.part = smem + a.smem_cells;
+    sg.cells = a.smem_cells;
     if (a.n_big > 0) {
         Grp gb;
         gb.block = true;
@@ -525,7 +566,7 @@ __global__ void __launch_bounds__(SN1D_THREADS) sn1d_kernel(Sn1dArgs a) {
             const int jb = job;
             __syncthreads();
             if (jb >= a.n_big) break;
-            dispatch<T, true>(a, gb, sg, a.big_list[jb]);
+            dispatch<T>(a, gb, sg, a.big_list[jb]);
         }
     }
     Grp gw;
@@ -540,7 +581,7 @@ __global__ void __launch_bounds__(SN1D_THREADS) sn1d_kernel(Sn1dArgs a) {
         if (lane == 0) jw = atomicAdd(a.counter, 1);
         jw = __shfl_sync(0xffffffffu, jw, 0);
         if (jw >= a.n_small) return;
-        dispatch<T, false>(a, gw, sg, a.order_list[jw]);
+        dispatch<T>(a, gw, sg, a.order_list[jw]);
     }
 }
 
@@ -587,7 +628,7 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
     void* p;
     NOP_TRY(ctx->scratch("sn1d_X", sizeof(Cell4<T>) * G * C, &p));
     Cell4<T>* X = (Cell4<T>*)p;
-    NOP_TRY(ctx->scratch("sn1d_U", sizeof(Cell2<T>) * G * C, &p));
+    NOP_TRY(ctx->scratch("sn1d_U", sizeof(Cell2<T>) * C, &p));
     Cell2<T>* U = (Cell2<T>*)p;
     NOP_TRY(ctx->scratch("sn1d_scat", sizeof(T) * (G > 1 ? (long long)G * G * C : 1), &p));
     T* scat = (T*)p;
@@ -604,9 +645,9 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
     NOP_TRY(ctx->scratch("sn1d_int", sizeof(int) * (5 * (size_t)B + 4), &p));
     int* ints = (int*)p;
     int* order_d = ints;
-    int* cfg_d = ints + B;
     int* it_d = ints + 2 * B;
     int* st_d = ints + 3 * B;
+    int* cfg_d = ints + B;
     int* big_d = ints + 4 * B;
     int* counter = ints + 5 * B;
     NOP_TRY(ctx->scratch("sn1d_outer", sizeof(int) * B, &p));
@@ -614,12 +655,17 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
     NOP_TRY(ctx->scratch("sn1d_dbl", sizeof(double) * 2 * (size_t)B, &p));
     double* ch_d = (double*)p;
     double* kk_d = ch_d + B;
+    unsigned long long* trace_d = nullptr;
+    if (ctx->timing) {
+        NOP_TRY(ctx->scratch("sn1d_trace", sizeof(unsigned long long) * 3 * (size_t)B, &p));
+        trace_d = (unsigned long long*)p;
+    }
 
     // ---- scheduling (host side).  Estimated work of an instance: cells x
     // angles x iterations, the iterations from the largest in-group
     // scattering ratio c (source iteration contracts roughly like c).  The
     // persistent grid has `warps_total` warps; an instance worth more than
-    // twice a warp's fair share of the batch runs on a whole block (its angles
+    // eight times a warp's fair share of the batch runs on a whole block (its angles
     // split over the block's warps) so that it does not set the critical path.
     const int blocks_max = ctx->sm_count * SN1D_BLOCKS_PER_SM;
     const double tol_its = eigen ? std::min(o->tol_inner, o->tol) : o->tol;
@@ -631,7 +677,7 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
         cost[b] = (double)s.ncell[b] * s.order[b] * its * G;
         total_cost += cost[b];
     }
-    const int max_smem_cells = (int)(SN1D_SMEM_BYTES / (3 * sizeof(T)));
+    const int max_smem_cells = (int)(SN1D_SMEM_BYTES / ((1 + SN1D_THREADS / 32) * sizeof(T)));
     const int warps_total =
         (int)std::max<long long>(1, std::min<long long>(B, (long long)blocks_max * (SN1D_THREADS / 32)));
     const double share = total_cost / warps_total;
@@ -639,8 +685,10 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
     int smem_cells = 1;
     for (int b = 0; b < B; ++b) {
         const int h = s.order[b] / 2;
-        const bool is_big = B > 1 && cost[b] > 2.0 * share && h >= SN1D_THREADS / 32 &&
-                            s.ncell[b] <= max_smem_cells;
+        const bool fits = h >= SN1D_THREADS / 32 && s.ncell[b] <= max_smem_cells;
+        const bool is_big =
+            fits && (o->schedule == NOP_SCHED_BLOCK ||
+                     (o->schedule == NOP_SCHED_AUTO && B > 1 && cost[b] > 8.0 * share));
         int lg, A;
         if (is_big) {
             const int hw = (h + SN1D_THREADS / 32 - 1) / (SN1D_THREADS / 32);
@@ -699,9 +747,9 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
     a.mu = s.mu_d;
     a.w = s.w_d;
     a.boff = s.boff_d;
-    a.cfg = cfg_d;
     a.X = X;
     a.U = U;
+    a.cfg = cfg_d;
     a.scat = scat;
     a.ext = ext;
     a.psib = psib;
@@ -722,11 +770,12 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
     a.ch_out = ch_d;
     a.k_out = kk_d;
     a.outer_out = outer_d;
+    a.trace = trace_d;
     const int blocks = (int)std::max<long long>(
         1, std::min<long long>(blocks_max, (long long)big.size() +
                                                ((long long)small.size() + SN1D_THREADS / 32 - 1) /
                                                    (SN1D_THREADS / 32)));
-    const size_t smem = 3 * sizeof(T) * (size_t)smem_cells;
+    const size_t smem = (1 + SN1D_THREADS / 32) * sizeof(T) * (size_t)smem_cells;
     NOP_CUDA_TRY(ctx, cudaFuncSetAttribute(sn1d_kernel<T>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)SN1D_SMEM_BYTES));
@@ -760,6 +809,25 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
         // the host vectors above are read by the copies: wait for them
         NOP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
         return NOP_OK;
+    }
+    if (trace_d) {
+        std::vector<unsigned long long> tr(3 * (size_t)B);
+        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(tr.data(), trace_d, sizeof(unsigned long long) * 3 * B,
+                                          cudaMemcpyDeviceToHost, ctx->stream));
+        NOP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        unsigned long long t0 = ~0ull, t1 = 0;
+        double mx = 0, sum = 0;
+        for (int b = 0; b < B; ++b) {
+            t0 = std::min(t0, tr[3 * b]);
+            t1 = std::max(t1, tr[3 * b + 1]);
+            const double d = (double)(tr[3 * b + 1] - tr[3 * b]) * 1e-6;
+            mx = std::max(mx, d);
+            sum += d;
+        }
+        ctx->trace_span_ms = (double)(t1 - t0) * 1e-6;
+        ctx->trace_max_ms = mx;
+        ctx->trace_mean_ms = sum / B;
+        ctx->trace_big = (int)big.size();
     }
     std::vector<int> it_h(B), st_h(B), out_h(B);
     std::vector<double> ch_h(B);
