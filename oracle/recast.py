@@ -22,10 +22,12 @@ Readings where the paper is silent (the CUDA side does the same):
     (trunk evaluated at bin centres); only the final flux is evaluated at the
     instance's cell centres.  FNO: the operator grid is the instance grid.
   * linear scaling: the trained operator saw sources normalised to unit
-    integral (Eq. 13).  A source s is applied as
-        sigma * (N[s+ / sigma] - N[s- / sigma]),  sigma = integral |s|,
-    s+ = max(s, 0), s- = max(-s, 0); a part that is identically zero is
-    skipped (a ReLU network maps 0 to a nonzero constant), sigma = 0 gives 0.
+    integral (Eq. 13), and the exact solution operator is linear.  A source s
+    is applied part by part, each part normalised to unit integral:
+        sigma+ N[s+ / sigma+] - sigma- N[s- / sigma-],
+    s+ = max(s, 0), s- = max(-s, 0), sigma+- = integral of s+-; a part with
+    zero integral contributes nothing (a ReLU network maps 0 to a nonzero
+    constant, so it is never evaluated on an empty part).
   * stopping: ||u_{k+1} - u_k||_2 / ||u_{k+1}||_2 <= tol or k = itmax;
     divergence: a non-finite iterate, or the absolute change ||u_{k+1} - u_k||_2
     failing to shrink for DIVERGE_RUN consecutive iterations (a fixed-point
@@ -55,30 +57,28 @@ def projection_matrix(edges, M, L):
 
 
 def _split_apply(apply_unit, s, cellsize):
-    """sigma * (N[s+/sigma] - N[s-/sigma]) over a batch s (B, ...)."""
-    out = None
-    sig = np.sum(np.abs(s) * cellsize, axis=tuple(range(1, s.ndim)))
+    """sigma+ N[s+/sigma+] - sigma- N[s-/sigma-] over a batch s (B, ...)."""
+    axes = tuple(range(1, s.ndim))
     res = []
     for b in range(s.shape[0]):
-        if sig[b] == 0:
-            res.append(None)
-            continue
-        pos = np.maximum(s[b], 0) / sig[b]
-        neg = np.maximum(-s[b], 0) / sig[b]
-        acc = 0.0
-        if np.any(pos > 0):
-            acc = acc + apply_unit(pos[None])[0]
-        if np.any(neg > 0):
-            acc = acc - apply_unit(neg[None])[0]
-        res.append(sig[b] * acc)
+        pos = np.maximum(s[b], 0)
+        neg = np.maximum(-s[b], 0)
+        sp = float(np.sum(pos) * cellsize)
+        sn = float(np.sum(neg) * cellsize)
+        acc = None
+        if sp > 0:
+            acc = sp * apply_unit((pos / sp)[None])[0]
+        if sn > 0:
+            t = sn * apply_unit((neg / sn)[None])[0]
+            acc = -t if acc is None else acc - t
+        res.append(acc)
     shape = None
     for r in res:
         if r is not None:
             shape = np.shape(r)
     if shape is None:
         return None
-    out = np.stack([np.zeros(shape) if r is None else np.broadcast_to(r, shape) for r in res])
-    return out
+    return np.stack([np.zeros(shape) if r is None else r for r in res])
 
 
 class DeepONetOp:
