@@ -207,6 +207,101 @@ int nop_solve_fixed_source(nop_ctx *ctx, const nop_solve_opts *opts,
 int nop_solve_eigen(nop_ctx *ctx, const nop_solve_opts *opts, const double *phi0,
                     double k0, double *phi_out, double *k_out, nop_stats *stats);
 
+/* ------------------------------------------------------ neural operator */
+
+#define NOP_NO_DEEPONET  1   /* Sec. 4.1, Eq. 11: <branch(sensors), trunk(x)>     */
+#define NOP_NO_FNO1D     2   /* Sec. 4.2: lift, Fourier layers, projection (1D)   */
+#define NOP_NO_FNO2D     3   /* the same on an x-y grid                           */
+
+/* Shape of the solution operator N trained at p* = (sigma_t*, sigma_s*)
+ * (Sec. 5.1 Eq. 19).  DeepONet: `sensors` uniform bins over [0, length]
+ * feed the branch MLP (widths sensors -> width x (depth-1) -> basis); the trunk
+ * MLP maps x/length (1 -> width x (depth-1) -> basis); ReLU after every hidden
+ * layer, none after the last.  FNO: the operator acts on the problem's own
+ * grid; `depth` Fourier layers of `width` channels keep `modes` modes (2D:
+ * modes x modes in each of the two k_y half-planes), projection width `proj`.
+ * Parameters are one FP32 array, concatenated in this order (W row-major
+ * [out][in]):
+ *   DeepONet: branch layer 0 W, b, ..., branch layer depth-1 W, b, then the
+ *             trunk layers the same way.
+ *   FNO1D:    lift W [width][2], b; per layer l: spectral re [modes][width][width],
+ *             im [same], pointwise W [width][width], b; proj1 W [proj][width],
+ *             b; proj2 W [1][proj], b.  Inputs per point: (S(x), x/length).
+ *   FNO2D:    lift W [width][3], b; per layer: re1, im1, re2, im2 each
+ *             [modes][modes][width][width] (blocks k_y < modes and k_y >= ny-modes),
+ *             pointwise W, b; proj1 W, b; proj2 W, b.  Inputs (S, x/lx, y/ly). */
+typedef struct {
+    int kind;
+    int sensors;
+    int width;
+    int basis;
+    int depth;
+    int modes;
+    int proj;
+    double sigma_t_star;
+    double sigma_s_star;
+    double length;
+} nop_no_config;
+
+/* Training options (App. A1, Table A1: MSE loss, Adam). */
+typedef struct {
+    int steps;               /* Adam steps                                       */
+    int batch;               /* samples per step                                 */
+    float lr, beta1, beta2, eps;
+    const int *order;        /* [steps * batch] sample indices (host), or NULL for
+                                sequential batches                              */
+} nop_train_config;
+
+/* Number of FP32 parameters of a configuration.  Errors: NOP_EINVAL. */
+int nop_no_param_count(const nop_no_config *cfg, long long *n);
+
+/* Install an operator and its parameters (host FP32 array in the order
+ * above); resets the Adam state.  Errors: NOP_EINVAL, NOP_ENOMEM, NOP_ECUDA. */
+int nop_no_set(nop_ctx *ctx, const nop_no_config *cfg, const float *params);
+
+/* Copy the current parameters into a host array of nop_no_param_count entries. */
+int nop_no_get(nop_ctx *ctx, float *params);
+
+/* Raw network forward on n samples (no scaling): DeepONet inputs [n][sensors],
+ * coords [n_coords] (x/length), out [n][n_coords]; FNO inputs [n][grid points]
+ * with the grid given by coords (1D: n_coords = grid size; 2D: the current
+ * x-y problem's nx * ny, coords ignored), out [n][grid points].  Host arrays. */
+int nop_no_forward(nop_ctx *ctx, int n, const float *inputs, const float *coords,
+                   int n_coords, float *out);
+
+/* MSE loss and its gradient with respect to every parameter (same layout as
+ * the parameters) for one batch, without updating anything.  Host arrays. */
+int nop_no_loss_grad(nop_ctx *ctx, int n, const float *inputs, const float *coords,
+                     int n_coords, const float *targets, double *loss, float *grad);
+
+/* Train with Adam on n samples (inputs/targets as in nop_no_loss_grad);
+ * loss_history (host, may be NULL) receives the loss of every step. */
+int nop_no_train(nop_ctx *ctx, const nop_train_config *tc, int n, const float *inputs,
+                 const float *coords, int n_coords, const float *targets,
+                 double *loss_history);
+
+/* Operator input map: average a cell field of the current slab problem (host
+ * [C] doubles, one group) over each instance's `sensors` bins, out [n_inst][sensors]. */
+int nop_no_sensors(nop_ctx *ctx, const double *field, float *out);
+
+/* One application of the trained operator to an isotropic source per
+ * instance of the current problem.  The network saw sources of unit integral
+ * (Eq. 13) and the exact solution operator is linear, so a source s is applied
+ * part by part as sigma+ N[s+/sigma+] - sigma- N[s-/sigma-], s+- its positive
+ * and negative parts, sigma+- their integrals (a part with zero integral is
+ * skipped).
+ * src, phi_out: host [C] doubles (one group). */
+int nop_no_predict(nop_ctx *ctx, const double *src, double *phi_out);
+
+/* Equation-recast iteration of Sec. 5.1 Eq. 24 for the current fixed-source
+ * problem (one group): phi <- N[S + ((Sigma_s - Sigma_s*) - (Sigma_t - Sigma_t*)) phi]
+ * from phi = 0, per instance until the relative change <= tol or itmax.
+ * phi_out: host [C] doubles (or device with NOP_OUT_DEVICE in flags); instances
+ * whose iteration diverged get the zero flux and status NOP_EDIVERGE.
+ * stats: recast_iterations / recast_status / inst_status are filled. */
+int nop_recast_iterate(nop_ctx *ctx, double tol, int itmax, int flags, double *phi_out,
+                       nop_stats *stats);
+
 /* --------------------------------------------------------------- tracing */
 
 /* Device-side phase times accumulated since timing was enabled. */

@@ -10,7 +10,48 @@ import numpy as np
 
 from . import capi
 from .capi import (NOP_BC_REFLECTIVE, NOP_BC_VACUUM, NOP_GEOM_SLAB, NOP_GEOM_XY,
-                   NOP_PREC_F32, NOP_PREC_F64, NOP_WARM_NONE, NOP_WARM_RECAST, NopError)
+                   NOP_NO_DEEPONET, NOP_NO_FNO1D, NOP_NO_FNO2D, NOP_PREC_F32, NOP_PREC_F64,
+                   NOP_WARM_NONE, NOP_WARM_RECAST, NopError)
+
+
+
+def no_config(kind, sensors=128, width=128, basis=128, depth=4, modes=16, proj=128,
+              sigma_t_star=1.0, sigma_s_star=0.5, length=10.0):
+    c = capi.nop_no_config()
+    c.kind, c.sensors, c.width, c.basis, c.depth = kind, sensors, width, basis, depth
+    c.modes, c.proj = modes, proj
+    c.sigma_t_star, c.sigma_s_star, c.length = sigma_t_star, sigma_s_star, length
+    return c
+
+
+def no_param_names(cfg):
+    """Tensor names in the flat parameter order of include/nop.h."""
+    names = []
+    if cfg.kind == NOP_NO_DEEPONET:
+        for net in ("b", "t"):
+            for l in range(cfg.depth):
+                names += ["%s%d.W" % (net, l), "%s%d.b" % (net, l)]
+    else:
+        names += ["lift.W", "lift.b"]
+        spec = ["re", "im"] if cfg.kind == NOP_NO_FNO1D else ["re1", "im1", "re2", "im2"]
+        for l in range(cfg.depth):
+            names += ["spec%d.%s" % (l, k) for k in spec] + ["pw%d.W" % l, "pw%d.b" % l]
+        names += ["proj1.W", "proj1.b", "proj2.W", "proj2.b"]
+    return names
+
+
+def flatten_params(cfg, params):
+    return np.concatenate([np.asarray(params[k], dtype=np.float32).reshape(-1)
+                           for k in no_param_names(cfg)])
+
+
+def unflatten_params(cfg, flat, like):
+    out, o = {}, 0
+    for k in no_param_names(cfg):
+        n = np.asarray(like[k]).size
+        out[k] = np.asarray(flat[o:o + n], dtype=np.float64).reshape(np.shape(like[k]))
+        o += n
+    return out
 
 __all__ = ["Solver", "NopError", "capi"]
 
@@ -68,6 +109,91 @@ class Solver:
         t = capi.nop_timings()
         self._check(self._L.nop_get_timing(self.h, C.byref(t)), "nop_get_timing")
         return {k: getattr(t, k) for k, _ in t._fields_}
+
+    # ---------------------------------------------------- neural operator
+    def no_set(self, cfg, params):
+        """Install an operator; params: dict of arrays (names of no_param_names)."""
+        flat = flatten_params(cfg, params)
+        n = C.c_longlong()
+        self._check(self._L.nop_no_param_count(C.byref(cfg), C.byref(n)), "nop_no_param_count")
+        if n.value != flat.size:
+            raise ValueError("parameter count %d != %d" % (flat.size, n.value))
+        self._check(self._L.nop_no_set(self.h, C.byref(cfg), capi._ptr(flat, capi._fp)),
+                    "nop_no_set")
+        self.no_cfg, self.no_like = cfg, {k: np.asarray(v) for k, v in params.items()}
+
+    def no_get(self):
+        n = C.c_longlong()
+        self._L.nop_no_param_count(C.byref(self.no_cfg), C.byref(n))
+        flat = np.zeros(n.value, dtype=np.float32)
+        self._check(self._L.nop_no_get(self.h, capi._ptr(flat, capi._fp)), "nop_no_get")
+        return unflatten_params(self.no_cfg, flat, self.no_like)
+
+    @staticmethod
+    def _f32(a):
+        return np.ascontiguousarray(a, dtype=np.float32)
+
+    def no_forward(self, inputs, coords=None, out_width=None):
+        U = self._f32(inputs)
+        X = None if coords is None else self._f32(coords)
+        n = U.shape[0]
+        nc = 0 if X is None else X.size
+        ow = out_width if out_width is not None else (nc if self.no_cfg.kind == NOP_NO_DEEPONET else U.shape[1])
+        out = np.zeros((n, ow), dtype=np.float32)
+        self._check(self._L.nop_no_forward(self.h, n, capi._ptr(U, capi._fp),
+                                           None if X is None else capi._ptr(X, capi._fp), nc,
+                                           capi._ptr(out, capi._fp)), "nop_no_forward")
+        return out
+
+    def no_loss_grad(self, inputs, targets, coords=None):
+        U, Y = self._f32(inputs), self._f32(targets)
+        X = None if coords is None else self._f32(coords)
+        nc = 0 if X is None else X.size
+        loss = C.c_double()
+        n = C.c_longlong()
+        self._L.nop_no_param_count(C.byref(self.no_cfg), C.byref(n))
+        g = np.zeros(n.value, dtype=np.float32)
+        self._check(self._L.nop_no_loss_grad(self.h, U.shape[0], capi._ptr(U, capi._fp),
+                                             None if X is None else capi._ptr(X, capi._fp), nc,
+                                             capi._ptr(Y, capi._fp), C.byref(loss),
+                                             capi._ptr(g, capi._fp)), "nop_no_loss_grad")
+        return loss.value, unflatten_params(self.no_cfg, g, self.no_like)
+
+    def no_train(self, inputs, targets, coords=None, steps=1000, batch=100, lr=1e-3,
+                 beta1=0.9, beta2=0.999, eps=1e-8, order=None):
+        U, Y = self._f32(inputs), self._f32(targets)
+        X = None if coords is None else self._f32(coords)
+        nc = 0 if X is None else X.size
+        tc = capi.nop_train_config()
+        tc.steps, tc.batch, tc.lr, tc.beta1, tc.beta2, tc.eps = steps, batch, lr, beta1, beta2, eps
+        ordr = None if order is None else np.ascontiguousarray(order, dtype=np.int32)
+        tc.order = None if ordr is None else capi._ptr(ordr, capi._ip)
+        hist = np.zeros(steps)
+        self._check(self._L.nop_no_train(self.h, C.byref(tc), U.shape[0], capi._ptr(U, capi._fp),
+                                         None if X is None else capi._ptr(X, capi._fp), nc,
+                                         capi._ptr(Y, capi._fp), capi._ptr(hist)), "nop_no_train")
+        return hist
+
+    def no_sensors(self, field):
+        f = capi._f64(field)
+        out = np.zeros((self.n_inst, self.no_cfg.sensors), dtype=np.float32)
+        self._check(self._L.nop_no_sensors(self.h, capi._ptr(f), capi._ptr(out, capi._fp)),
+                    "nop_no_sensors")
+        return out
+
+    def no_predict(self, src):
+        s = capi._f64(src)
+        out = np.zeros(self.G * self.C)
+        self._check(self._L.nop_no_predict(self.h, capi._ptr(s), capi._ptr(out)), "nop_no_predict")
+        return out
+
+    def recast_iterate(self, tol=1e-4, itmax=200):
+        out = np.zeros(self.G * self.C)
+        st, it, ss = self._stats()
+        self._check(self._L.nop_recast_iterate(self.h, tol, itmax, 0, out.ctypes.data,
+                                               C.byref(st)), "nop_recast_iterate")
+        return out, {"iterations": it, "status": ss, "max_iterations": st.recast_iterations,
+                     "recast_status": st.recast_status}
 
     # ---------------------------------------------------------- problems
     def set_slabs(self, n_cells, width, order, sigma_t, sigma_s, source=None,

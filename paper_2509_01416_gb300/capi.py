@@ -56,6 +56,24 @@ class nop_timings(C.Structure):
                 ("last_inst_mean_ms", C.c_double), ("last_block_instances", C.c_int)]
 
 
+NOP_NO_DEEPONET, NOP_NO_FNO1D, NOP_NO_FNO2D = 1, 2, 3
+
+
+class nop_no_config(C.Structure):
+    _fields_ = [("kind", C.c_int), ("sensors", C.c_int), ("width", C.c_int),
+                ("basis", C.c_int), ("depth", C.c_int), ("modes", C.c_int),
+                ("proj", C.c_int), ("sigma_t_star", C.c_double),
+                ("sigma_s_star", C.c_double), ("length", C.c_double)]
+
+
+class nop_train_config(C.Structure):
+    _fields_ = [("steps", C.c_int), ("batch", C.c_int), ("lr", C.c_float),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("order", _ip)]
+
+
+_fp = C.POINTER(C.c_float)
+
 # every symbol include/nop.h declares, with its ctypes signature
 SIGNATURES = {
     "nop_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int]),
@@ -68,6 +86,18 @@ SIGNATURES = {
     "nop_solve_fixed_source": (C.c_int, [C.c_void_p, C.POINTER(nop_solve_opts), C.c_void_p,
                                          C.c_void_p, C.POINTER(nop_stats)]),
     "nop_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "nop_no_param_count": (C.c_int, [C.POINTER(nop_no_config), C.POINTER(C.c_longlong)]),
+    "nop_no_set": (C.c_int, [C.c_void_p, C.POINTER(nop_no_config), _fp]),
+    "nop_no_get": (C.c_int, [C.c_void_p, _fp]),
+    "nop_no_forward": (C.c_int, [C.c_void_p, C.c_int, _fp, _fp, C.c_int, _fp]),
+    "nop_no_loss_grad": (C.c_int, [C.c_void_p, C.c_int, _fp, _fp, C.c_int, _fp,
+                                   C.POINTER(C.c_double), _fp]),
+    "nop_no_train": (C.c_int, [C.c_void_p, C.POINTER(nop_train_config), C.c_int, _fp, _fp,
+                               C.c_int, _fp, _dp]),
+    "nop_no_sensors": (C.c_int, [C.c_void_p, _dp, _fp]),
+    "nop_no_predict": (C.c_int, [C.c_void_p, _dp, _dp]),
+    "nop_recast_iterate": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_void_p,
+                                     C.POINTER(nop_stats)]),
     "nop_get_timing": (C.c_int, [C.c_void_p, C.POINTER(nop_timings)]),
     "nop_solve_eigen": (C.c_int, [C.c_void_p, C.POINTER(nop_solve_opts), C.c_void_p,
                                   C.c_double, C.c_void_p, C.c_void_p,

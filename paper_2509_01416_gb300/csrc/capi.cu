@@ -294,6 +294,8 @@ int nop_set_problem(nop_ctx* ctx, const nop_problem* p) {
         s.nang_d = (int*)d;
         NOP_TRY(upload(ctx, "dx", dx.data(), sizeof(double) * B, &d));
         s.dx_d = (double*)d;
+        NOP_TRY(upload(ctx, "width", s.width.data(), sizeof(double) * B, &d));
+        s.width_d = (double*)d;
         NOP_TRY(upload(ctx, "boff", boff.data(), sizeof(long long) * B, &d));
         s.boff_d = (long long*)d;
         NOP_TRY(nop::build_gauss_legendre(ctx));   // synchronises the stream
@@ -362,14 +364,32 @@ int nop_solve_fixed_source(nop_ctx* ctx, const nop_solve_opts* o, const double* 
         st->recast_iterations = 0;
         st->recast_status = NOP_OK;
     }
-    if (o->warm_start != NOP_WARM_NONE) {
-        ctx->set_error("warm start requested but no neural operator is loaded");
-        return NOP_ESTATE;
+    bool phi0_dev = (o->flags & NOP_PHI0_DEVICE) != 0;
+    if (o->warm_start == NOP_WARM_RECAST) {
+        // Eq. 9a / Eq. 20: the recast prediction (Eq. 24) is the initial guess
+        if (!ctx->no.loaded) {
+            ctx->set_error("warm start requested but no neural operator is loaded");
+            return NOP_ESTATE;
+        }
+        nop_stats rs{};
+        void* p;
+        NOP_TRY(ctx->scratch("ws_phi0", sizeof(double) * ctx->C, &p));
+        NOP_TRY(nop_recast_iterate(ctx, o->recast_tol > 0 ? o->recast_tol : 1e-4,
+                                   o->recast_itmax > 0 ? o->recast_itmax : 200, NOP_OUT_DEVICE,
+                                   (double*)p, &rs));
+        phi0 = (const double*)p;
+        phi0_dev = true;
+        if (st) {
+            st->recast_iterations = rs.recast_iterations;
+            st->recast_status = rs.recast_status;
+        }
+    } else if (o->warm_start != NOP_WARM_NONE) {
+        ctx->set_error("unknown warm start");
+        return NOP_EINVAL;
     }
     if (ctx->geometry == NOP_GEOM_SLAB)
-        return nop::sn1d_solve(ctx, o, false, phi0, (o->flags & NOP_PHI0_DEVICE) != 0,
-                               nullptr, phi_out, (o->flags & NOP_OUT_DEVICE) != 0,
-                               nullptr, st);
+        return nop::sn1d_solve(ctx, o, false, phi0, phi0_dev, nullptr, phi_out,
+                               (o->flags & NOP_OUT_DEVICE) != 0, nullptr, st);
     ctx->set_error("x-y solver not available");
     return NOP_EINVAL;
 }

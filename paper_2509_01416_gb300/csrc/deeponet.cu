@@ -1,0 +1,582 @@
+// DeepONet solution operator (Sec. 4.1, Eq. 11) and the equation-recast
+// iteration around it (Sec. 3.1 Eq. 7, Sec. 3.2 Eq. 8, Sec. 5.1 Eq. 24).
+//
+// Network: branch MLP on `sensors` source values, trunk MLP on x/length,
+// output <branch, trunk>; ReLU after hidden layers.  All matrix products run
+// on the BF16 tensor-core GEMM of nn_kernels.cu with FP32 accumulation.
+//
+// Recast on a batch of slabs: the operator lives on its own grid of M bins
+// over [0, L]; each instance's source S and mismatch
+// delta = (Sigma_s - Sigma_s*) - (Sigma_t - Sigma_t*) are averaged onto the
+// bins (overlap weights) once, then every iteration applies the operator to
+// src = P S + (P delta) u through the linear scaling
+// sigma+ N[src+/sigma+] - sigma- N[src-/sigma-] (each signed part at unit
+// integral, sigma+- = h sum max(+-src, 0)), giving branch
+// coefficients beta and u_new = T_ref beta with T_ref the trunk at the bin
+// centres.  Converged instances freeze.  The final flux at the instance's own
+// cell centres is beta . trunk(x_c).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "nn_kernels.cuh"
+
+namespace nop {
+
+int no_layout(const nop_no_config* c, std::vector<long long>* off, std::vector<long long>* len,
+              long long* total) {
+    off->clear();
+    len->clear();
+    long long o = 0;
+    auto push = [&](long long n) {
+        off->push_back(o);
+        len->push_back(n);
+        o += n;
+    };
+    if (c->width < 1 || c->depth < 1) return NOP_EINVAL;
+    if (c->kind == NOP_NO_DEEPONET) {
+        if (c->sensors < 1 || c->basis < 1 || c->depth < 2) return NOP_EINVAL;
+        for (int net = 0; net < 2; ++net)
+            for (int l = 0; l < c->depth; ++l) {
+                const int in = l == 0 ? (net == 0 ? c->sensors : 1) : c->width;
+                const int out = l == c->depth - 1 ? c->basis : c->width;
+                push((long long)out * in);
+                push(out);
+            }
+    } else if (c->kind == NOP_NO_FNO1D || c->kind == NOP_NO_FNO2D) {
+        if (c->modes < 1 || c->proj < 1) return NOP_EINVAL;
+        const int W = c->width, in_ch = c->kind == NOP_NO_FNO1D ? 2 : 3;
+        push((long long)W * in_ch);
+        push(W);
+        for (int l = 0; l < c->depth; ++l) {
+            const long long spec = c->kind == NOP_NO_FNO1D
+                                       ? (long long)c->modes * W * W
+                                       : (long long)c->modes * c->modes * W * W;
+            const int nspec = c->kind == NOP_NO_FNO1D ? 2 : 4;
+            for (int k = 0; k < nspec; ++k) push(spec);
+            push((long long)W * W);
+            push(W);
+        }
+        push((long long)c->proj * W);
+        push(c->proj);
+        push(c->proj);
+        push(1);
+    } else {
+        return NOP_EINVAL;
+    }
+    *total = o;
+    return NOP_OK;
+}
+
+namespace {
+
+// tensor index of layer l of net (0 branch, 1 trunk): W at 2*(net*depth+l), b at +1
+inline const float* Wp(nop_ctx* ctx, int net, int l) {
+    return ctx->no.params + ctx->no.off[2 * (net * ctx->no.cfg.depth + l)];
+}
+inline const float* Bp(nop_ctx* ctx, int net, int l) {
+    return ctx->no.params + ctx->no.off[2 * (net * ctx->no.cfg.depth + l) + 1];
+}
+inline float* dWp(nop_ctx* ctx, int net, int l) {
+    return ctx->no.grad + ctx->no.off[2 * (net * ctx->no.cfg.depth + l)];
+}
+inline float* dBp(nop_ctx* ctx, int net, int l) {
+    return ctx->no.grad + ctx->no.off[2 * (net * ctx->no.cfg.depth + l) + 1];
+}
+inline int dim_in(const nop_no_config& c, int net, int l) {
+    return l == 0 ? (net == 0 ? c.sensors : 1) : c.width;
+}
+inline int dim_out(const nop_no_config& c, int l) { return l == c.depth - 1 ? c.basis : c.width; }
+
+// activation buffers of one net: A[l], Z[l] of rows x width (max)
+int acts(nop_ctx* ctx, int net, int rows, std::vector<float*>* A, std::vector<float*>* Z) {
+    const nop_no_config& c = ctx->no.cfg;
+    const int wmax = c.width > c.basis ? c.width : c.basis;
+    A->resize(c.depth);
+    Z->resize(c.depth);
+    for (int l = 0; l < c.depth; ++l) {
+        char na[32], nz[32];
+        snprintf(na, sizeof na, "don_A%d_%d", net, l);
+        snprintf(nz, sizeof nz, "don_Z%d_%d", net, l);
+        void* p;
+        NOP_TRY(ctx->scratch(na, sizeof(float) * (size_t)rows * wmax, &p));
+        (*A)[l] = (float*)p;
+        NOP_TRY(ctx->scratch(nz, sizeof(float) * (size_t)rows * wmax, &p));
+        (*Z)[l] = (float*)p;
+    }
+    return NOP_OK;
+}
+
+int mlp_forward(nop_ctx* ctx, int net, int rows, const float* X, float** out, bool keep) {
+    const nop_no_config& c = ctx->no.cfg;
+    std::vector<float*> A, Z;
+    NOP_TRY(acts(ctx, net, rows, &A, &Z));
+    const float* h = X;
+    for (int l = 0; l < c.depth; ++l) {
+        const bool relu = l < c.depth - 1;
+        NOP_TRY(linear(ctx, rows, dim_in(c, net, l), dim_out(c, l), h, Wp(ctx, net, l),
+                       Bp(ctx, net, l), A[l], keep ? Z[l] : nullptr, relu));
+        h = A[l];
+    }
+    *out = A[c.depth - 1];
+    return NOP_OK;
+}
+
+int mlp_backward(nop_ctx* ctx, int net, int rows, const float* X, const float* dout) {
+    const nop_no_config& c = ctx->no.cfg;
+    std::vector<float*> A, Z;
+    NOP_TRY(acts(ctx, net, rows, &A, &Z));
+    void* p;
+    const int wmax = c.width > c.basis ? c.width : c.basis;
+    NOP_TRY(ctx->scratch(net ? "don_gT0" : "don_gB0", sizeof(float) * (size_t)rows * wmax, &p));
+    float* g0 = (float*)p;
+    NOP_TRY(ctx->scratch(net ? "don_gT1" : "don_gB1", sizeof(float) * (size_t)rows * wmax, &p));
+    float* g1 = (float*)p;
+    const float* g = dout;
+    for (int l = c.depth - 1; l >= 0; --l) {
+        const int in = dim_in(c, net, l), out = dim_out(c, l);
+        const float* dZ = g;
+        if (l < c.depth - 1) {
+            float* t = (g == g0) ? g1 : g0;
+            NOP_TRY(relu_backward(ctx, (long long)rows * out, g, Z[l], t));
+            dZ = t;
+        }
+        const float* hin = l == 0 ? X : A[l - 1];
+        GemmArgs w{};
+        w.M = out;
+        w.N = in;
+        w.K = rows;
+        w.A = dZ;
+        w.lda = out;
+        w.transA = 1;
+        w.B = hin;
+        w.ldb = in;
+        w.transB = 0;
+        w.C = dWp(ctx, net, l);
+        w.ldc = in;
+        w.alpha = 1.f;
+        NOP_TRY(gemm(ctx, w));
+        NOP_TRY(colsum(ctx, rows, out, dZ, dBp(ctx, net, l), false));
+        if (l > 0) {
+            float* t = (dZ == g0) ? g1 : g0;
+            GemmArgs d{};
+            d.M = rows;
+            d.N = in;
+            d.K = out;
+            d.A = dZ;
+            d.lda = out;
+            d.B = Wp(ctx, net, l);
+            d.ldb = in;
+            d.transB = 0;
+            d.C = t;
+            d.ldc = in;
+            d.alpha = 1.f;
+            NOP_TRY(gemm(ctx, d));
+            g = t;
+        }
+    }
+    return NOP_OK;
+}
+
+// ------------------------------------------------------------ recast kernels
+// Overlap-weighted bin average of a cell field: bins of width h = L/M, cells
+// of width dx = L/I of instance b.  f(c) is read through `mode`: 0 the field
+// itself, 1 the recast mismatch (Sigma_s - Sigma_s*) - (Sigma_t - Sigma_t*).
+__global__ void project_kernel(int B, int M, const long long* cell_off, const int* ncell,
+                               const double* width, const double* field, const double* sigt,
+                               const double* sigs, double st_star, double ss_star, int mode,
+                               float* out) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= (long long)B * M) return;
+    const int b = (int)(e / M), m = (int)(e % M);
+    const int I = ncell[b];
+    const double L = width[b], h = L / M, dx = L / I;
+    const double lo = m * h, hi = (m + 1) * h;
+    int i0 = (int)floor(lo / dx);
+    int i1 = (int)floor(hi / dx);
+    i0 = max(0, min(I - 1, i0));
+    i1 = max(0, min(I - 1, i1));
+    double acc = 0.0;
+    for (int i = i0; i <= i1; ++i) {
+        const double ov = fmin(hi, (i + 1) * dx) - fmax(lo, i * dx);
+        if (ov <= 0.0) continue;
+        const long long c = cell_off[b] + i;
+        const double f = mode == 0 ? field[c] : (sigs[c] - ss_star) - (sigt[c] - st_star);
+        acc += ov * f;
+    }
+    out[e] = (float)(acc / h);
+}
+
+// Split and scale the bin sources of every instance (one block per instance):
+// src = PS + PD * u;  sigma+- = h sum max(+-src, 0);  rows 2b / 2b+1 of U are
+// src+/sigma+ and src-/sigma- (each part at unit integral, as in training).
+__global__ void split_kernel(int M, double h, const float* PS, const float* PD, const float* u,
+                             float* U, float* sig, int* flags) {
+    __shared__ double red[2][32];
+    const int b = blockIdx.x;
+    double ap = 0.0, an = 0.0;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        const float s = PS[(long long)b * M + m] + PD[(long long)b * M + m] * u[(long long)b * M + m];
+        if (s > 0.f) ap += s;
+        else an -= s;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ap += __shfl_xor_sync(0xffffffffu, ap, o);
+        an += __shfl_xor_sync(0xffffffffu, an, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = ap;
+        red[1][threadIdx.x >> 5] = an;
+    }
+    __syncthreads();
+    double sp = 0.0, sn = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        sp += red[0][w];
+        sn += red[1][w];
+    }
+    sp *= h;
+    sn *= h;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        const float s = PS[(long long)b * M + m] + PD[(long long)b * M + m] * u[(long long)b * M + m];
+        U[(2LL * b) * M + m] = sp > 0 ? (float)(fmax((double)s, 0.0) / sp) : 0.f;
+        U[(2LL * b + 1) * M + m] = sn > 0 ? (float)(fmax(-(double)s, 0.0) / sn) : 0.f;
+    }
+    if (threadIdx.x == 0) {
+        sig[2 * b] = (float)sp;
+        sig[2 * b + 1] = (float)sn;
+        flags[b] = (sp > 0 ? 1 : 0) | (sn > 0 ? 2 : 0);
+    }
+}
+
+// beta_b = sigma+ N[+] - sigma- N[-] from the branch outputs of rows 2b, 2b+1
+__global__ void beta_kernel(int B, int p, const float* Bn, const float* sig, const int* flags,
+                            float* beta) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= (long long)B * p) return;
+    const int b = (int)(e / p), k = (int)(e % p);
+    const int f = flags[b];
+    float v = 0.f;
+    if (f & 1) v += sig[2 * b] * Bn[(2LL * b) * p + k];
+    if (f & 2) v -= sig[2 * b + 1] * Bn[(2LL * b + 1) * p + k];
+    beta[e] = v;
+}
+
+// Convergence bookkeeping of one recast iteration (one block per instance).
+// status: 0 running, 1 converged, 2 not converged (cap), 3 diverged.
+__global__ void recast_update_kernel(int M, int p, double tol, int diverge_run, const float* unew,
+                                     float* u, const float* beta, float* beta_keep, int* status,
+                                     int* iters, double* prev, int* run, int* active) {
+    __shared__ double red[2][32];
+    const int b = blockIdx.x;
+    if (status[b] != 0) return;
+    double d2 = 0.0, n2 = 0.0;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        const double a = unew[(long long)b * M + m], o = u[(long long)b * M + m];
+        d2 += (a - o) * (a - o);
+        n2 += a * a;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+        n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = d2;
+        red[1][threadIdx.x >> 5] = n2;
+    }
+    __syncthreads();
+    double D = 0.0, Nn = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        D += red[0][w];
+        Nn += red[1][w];
+    }
+    for (int m = threadIdx.x; m < M; m += blockDim.x) u[(long long)b * M + m] = unew[(long long)b * M + m];
+    for (int k = threadIdx.x; k < p; k += blockDim.x)
+        beta_keep[(long long)b * p + k] = beta[(long long)b * p + k];
+    if (threadIdx.x == 0) {
+        iters[b] += 1;
+        const double ab = sqrt(D);
+        const double ch = Nn > 0 ? ab / sqrt(Nn) : 0.0;
+        int st = 0;
+        if (!isfinite(ch) || !isfinite(Nn)) {
+            st = 3;
+        } else if (ch <= tol) {
+            st = 1;
+        } else {
+            run[b] = ab >= prev[b] ? run[b] + 1 : 0;
+            prev[b] = ab;
+            if (run[b] >= diverge_run) st = 3;
+        }
+        status[b] = st;
+        if (st == 0) atomicAdd(active, 1);
+    }
+}
+
+// Trunk input column and owning instance of global cells [c0, c0 + n).
+__global__ void cell_points_kernel(long long c0, int n, int B, const long long* cell_off,
+                                   const int* ncell, float* X, int* inst) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const long long c = c0 + k;
+    int lo = 0, hi = B - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (cell_off[mid] <= c) lo = mid;
+        else hi = mid - 1;
+    }
+    const int i = (int)(c - cell_off[lo]);
+    X[k] = (float)((i + 0.5) / ncell[lo]);
+    inst[k] = lo;
+}
+
+// phi_c = beta_inst(c) . t(x_c), operands rounded to BF16 like the GEMMs
+__global__ void trunk_dot_kernel(long long c0, int n, int p, const float* Tn, const int* inst,
+                                 const float* beta_keep, const int* status, double* phi) {
+    const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (k >= n) return;
+    const int b = inst[k];
+    float acc = 0.f;
+    if (!status || status[b] != 3)
+        for (int j = lane; j < p; j += 32)
+            acc += __bfloat162float(__float2bfloat16_rn(beta_keep[(long long)b * p + j])) *
+                   __bfloat162float(__float2bfloat16_rn(Tn[(long long)k * p + j]));
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) phi[c0 + k] = acc;
+}
+
+__global__ void bin_centres_kernel(int M, float* X) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < M) X[m] = (float)((m + 0.5) / M);
+}
+
+}  // namespace
+
+int deeponet_forward_raw(nop_ctx* ctx, int n, const float* U, int P, const float* X,
+                         float* out, bool keep) {
+    float *Bn, *Tn;
+    NOP_TRY(mlp_forward(ctx, 0, n, U, &Bn, keep));
+    NOP_TRY(mlp_forward(ctx, 1, P, X, &Tn, keep));
+    GemmArgs g{};
+    g.M = n;
+    g.N = P;
+    g.K = ctx->no.cfg.basis;
+    g.A = Bn;
+    g.lda = ctx->no.cfg.basis;
+    g.B = Tn;
+    g.ldb = ctx->no.cfg.basis;
+    g.transB = 1;
+    g.C = out;
+    g.ldc = P;
+    g.alpha = 1.f;
+    return gemm(ctx, g);
+}
+
+// Backward of the last deeponet_forward_raw(keep = true) for dL/dout (n x P).
+int deeponet_backward(nop_ctx* ctx, int n, int P, const float* dout, const float* U,
+                      const float* X) {
+    const nop_no_config& c = ctx->no.cfg;
+    std::vector<float*> Ab, Zb, At, Zt;
+    NOP_TRY(acts(ctx, 0, n, &Ab, &Zb));
+    NOP_TRY(acts(ctx, 1, P, &At, &Zt));
+    const float* Bn = Ab[c.depth - 1];
+    const float* Tn = At[c.depth - 1];
+    void* p;
+    NOP_TRY(ctx->scratch("don_dBn", sizeof(float) * (size_t)n * c.basis, &p));
+    float* dBn = (float*)p;
+    NOP_TRY(ctx->scratch("don_dTn", sizeof(float) * (size_t)P * c.basis, &p));
+    float* dTn = (float*)p;
+    GemmArgs g{};
+    g.M = n;
+    g.N = c.basis;
+    g.K = P;
+    g.A = dout;
+    g.lda = P;
+    g.B = Tn;
+    g.ldb = c.basis;
+    g.transB = 0;
+    g.C = dBn;
+    g.ldc = c.basis;
+    g.alpha = 1.f;
+    NOP_TRY(gemm(ctx, g));
+    GemmArgs h{};
+    h.M = P;
+    h.N = c.basis;
+    h.K = n;
+    h.A = dout;
+    h.lda = P;
+    h.transA = 1;
+    h.B = Bn;
+    h.ldb = c.basis;
+    h.C = dTn;
+    h.ldc = c.basis;
+    h.alpha = 1.f;
+    NOP_TRY(gemm(ctx, h));
+    NOP_TRY(mlp_backward(ctx, 0, n, U, dBn));
+    NOP_TRY(mlp_backward(ctx, 1, P, X, dTn));
+    return NOP_OK;
+}
+
+// Operator input map of a host cell field: bin averages per instance.
+int deeponet_project(nop_ctx* ctx, const double* field_host, float* out_host) {
+    SlabDev& s = ctx->slab;
+    const int B = s.n_inst, M = ctx->no.cfg.sensors;
+    void* q;
+    NOP_TRY(ctx->scratch("pj_field", sizeof(double) * (size_t)s.C, &q));
+    double* f = (double*)q;
+    NOP_TRY(ctx->scratch("pj_out", sizeof(float) * (size_t)B * M, &q));
+    float* o = (float*)q;
+    NOP_CUDA_TRY(ctx, cudaMemcpyAsync(f, field_host, sizeof(double) * (size_t)s.C,
+                                      cudaMemcpyHostToDevice, ctx->stream));
+    const long long BM_ = (long long)B * M;
+    project_kernel<<<(int)((BM_ + 255) / 256), 256, 0, ctx->stream>>>(
+        B, M, s.cell_off_d, s.ncell_d, s.width_d, f, nullptr, nullptr, 0.0, 0.0, 0, o);
+    NOP_CUDA_TRY(ctx, cudaGetLastError());
+    ctx->count_launch(false);
+    NOP_CUDA_TRY(ctx, cudaMemcpyAsync(out_host, o, sizeof(float) * BM_, cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+    NOP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return NOP_OK;
+}
+
+// Batched recast (predict_only: one operator application to src_d instead).
+// phi_d: device [C] doubles.  status_d / iters_d: device [B] (may be null).
+int deeponet_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* status_d,
+                    int* iters_d, bool predict_only, const double* src_d) {
+    const nop_no_config& c = ctx->no.cfg;
+    SlabDev& s = ctx->slab;
+    const int B = s.n_inst, M = c.sensors, p = c.basis;
+    const double h = c.length / M;
+    void* q;
+    NOP_TRY(ctx->scratch("rc_PS", sizeof(float) * (size_t)B * M, &q));
+    float* PS = (float*)q;
+    NOP_TRY(ctx->scratch("rc_PD", sizeof(float) * (size_t)B * M, &q));
+    float* PD = (float*)q;
+    NOP_TRY(ctx->scratch("rc_u", sizeof(float) * (size_t)B * M, &q));
+    float* u = (float*)q;
+    NOP_TRY(ctx->scratch("rc_unew", sizeof(float) * (size_t)B * M, &q));
+    float* unew = (float*)q;
+    NOP_TRY(ctx->scratch("rc_U", sizeof(float) * (size_t)2 * B * M, &q));
+    float* Usp = (float*)q;
+    NOP_TRY(ctx->scratch("rc_sig", sizeof(float) * 2 * (size_t)B, &q));
+    float* sig = (float*)q;
+    NOP_TRY(ctx->scratch("rc_beta", sizeof(float) * (size_t)B * p, &q));
+    float* beta = (float*)q;
+    NOP_TRY(ctx->scratch("rc_betak", sizeof(float) * (size_t)B * p, &q));
+    float* beta_keep = (float*)q;
+    NOP_TRY(ctx->scratch("rc_int", sizeof(int) * (size_t)(4 * B + 4), &q));
+    int* flags = (int*)q;
+    int* status = flags + B;
+    int* iters = flags + 2 * B;
+    int* run = flags + 3 * B;
+    int* active = flags + 4 * B;
+    NOP_TRY(ctx->scratch("rc_prev", sizeof(double) * (size_t)B, &q));
+    double* prev = (double*)q;
+    NOP_TRY(ctx->scratch("rc_Xb", sizeof(float) * (size_t)M, &q));
+    float* Xb = (float*)q;
+    NOP_TRY(ctx->scratch("rc_Tref", sizeof(float) * (size_t)M * p, &q));
+    float* Tref = (float*)q;
+
+    const int mk = ctx->phase_begin(1);
+    const long long BM_ = (long long)B * M;
+    project_kernel<<<(int)((BM_ + 255) / 256), 256, 0, ctx->stream>>>(
+        B, M, s.cell_off_d, s.ncell_d, s.width_d, predict_only ? src_d : ctx->src_d,
+        ctx->sigt_d, ctx->sigs_d, c.sigma_t_star, c.sigma_s_star, 0, PS);
+    NOP_CUDA_TRY(ctx, cudaGetLastError());
+    project_kernel<<<(int)((BM_ + 255) / 256), 256, 0, ctx->stream>>>(
+        B, M, s.cell_off_d, s.ncell_d, s.width_d, nullptr, ctx->sigt_d, ctx->sigs_d,
+        c.sigma_t_star, c.sigma_s_star, 1, PD);
+    NOP_CUDA_TRY(ctx, cudaGetLastError());
+    ctx->count_launch(false);
+    ctx->count_launch(false);
+    if (predict_only) NOP_CUDA_TRY(ctx, cudaMemsetAsync(PD, 0, sizeof(float) * BM_, ctx->stream));
+    NOP_CUDA_TRY(ctx, cudaMemsetAsync(u, 0, sizeof(float) * BM_, ctx->stream));
+    NOP_CUDA_TRY(ctx, cudaMemsetAsync(flags, 0, sizeof(int) * (size_t)(4 * B + 4), ctx->stream));
+    NOP_CUDA_TRY(ctx, cudaMemsetAsync(prev, 0x7f, sizeof(double) * (size_t)B, ctx->stream));
+    NOP_CUDA_TRY(ctx, cudaMemsetAsync(beta_keep, 0, sizeof(float) * (size_t)B * p, ctx->stream));
+    // trunk at the bin centres
+    bin_centres_kernel<<<(M + 127) / 128, 128, 0, ctx->stream>>>(M, Xb);
+    NOP_CUDA_TRY(ctx, cudaGetLastError());
+    ctx->count_launch(false);
+    float* Tn;
+    NOP_TRY(mlp_forward(ctx, 1, M, Xb, &Tn, false));
+    NOP_CUDA_TRY(ctx, cudaMemcpyAsync(Tref, Tn, sizeof(float) * (size_t)M * p,
+                                      cudaMemcpyDeviceToDevice, ctx->stream));
+    int* active_h = nullptr;
+    NOP_CUDA_TRY(ctx, cudaMallocHost(&active_h, sizeof(int)));
+    const int imax = predict_only ? 1 : itmax;
+    int it = 0;
+    int rc = NOP_OK;
+    for (it = 1; it <= imax; ++it) {
+        split_kernel<<<B, 128, 0, ctx->stream>>>(M, h, PS, PD, u, Usp, sig, flags);
+        if (cudaGetLastError() != cudaSuccess) { rc = NOP_ECUDA; break; }
+        ctx->count_launch(false);
+        float* Bn;
+        if ((rc = mlp_forward(ctx, 0, 2 * B, Usp, &Bn, false)) != NOP_OK) break;
+        beta_kernel<<<(int)(((long long)B * p + 255) / 256), 256, 0, ctx->stream>>>(B, p, Bn, sig,
+                                                                                  flags, beta);
+        if (cudaGetLastError() != cudaSuccess) { rc = NOP_ECUDA; break; }
+        ctx->count_launch(false);
+        GemmArgs g{};
+        g.M = B;
+        g.N = M;
+        g.K = p;
+        g.A = beta;
+        g.lda = p;
+        g.B = Tref;
+        g.ldb = p;
+        g.transB = 1;
+        g.C = unew;
+        g.ldc = M;
+        g.alpha = 1.f;
+        if ((rc = gemm(ctx, g)) != NOP_OK) break;
+        if (cudaMemsetAsync(active, 0, sizeof(int), ctx->stream) != cudaSuccess) { rc = NOP_ECUDA; break; }
+        recast_update_kernel<<<B, 128, 0, ctx->stream>>>(M, p, predict_only ? 1e300 : tol, 5, unew,
+                                                        u, beta, beta_keep, status, iters, prev,
+                                                        run, active);
+        if (cudaGetLastError() != cudaSuccess) { rc = NOP_ECUDA; break; }
+        ctx->count_launch(false);
+        if (cudaMemcpyAsync(active_h, active, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+            rc = NOP_ECUDA;
+            break;
+        }
+        if (*active_h == 0) break;
+    }
+    cudaFreeHost(active_h);
+    if (rc != NOP_OK) {
+        ctx->set_error("recast iteration failed");
+        return rc;
+    }
+    // final flux at every cell centre, in chunks of points
+    const long long C = s.C;
+    const int CH = 1 << 16;
+    NOP_TRY(ctx->scratch("rc_Xc", sizeof(float) * CH, &q));
+    float* Xc = (float*)q;
+    NOP_TRY(ctx->scratch("rc_inst", sizeof(int) * CH, &q));
+    int* inst = (int*)q;
+    for (long long c0 = 0; c0 < C; c0 += CH) {
+        const int n = (int)std::min<long long>(CH, C - c0);
+        cell_points_kernel<<<(n + 255) / 256, 256, 0, ctx->stream>>>(c0, n, B, s.cell_off_d,
+                                                                    s.ncell_d, Xc, inst);
+        NOP_CUDA_TRY(ctx, cudaGetLastError());
+        ctx->count_launch(false);
+        float* Tc;
+        NOP_TRY(mlp_forward(ctx, 1, n, Xc, &Tc, false));
+        trunk_dot_kernel<<<(n + 7) / 8, 256, 0, ctx->stream>>>(c0, n, p, Tc, inst, beta_keep,
+                                                               status, phi_d);
+        NOP_CUDA_TRY(ctx, cudaGetLastError());
+        ctx->count_launch(false);
+    }
+    ctx->phase_end(mk);
+    if (status_d)
+        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(status_d, status, sizeof(int) * B,
+                                          cudaMemcpyDeviceToDevice, ctx->stream));
+    if (iters_d)
+        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(iters_d, iters, sizeof(int) * B,
+                                          cudaMemcpyDeviceToDevice, ctx->stream));
+    return NOP_OK;
+}
+
+}  // namespace nop

@@ -32,6 +32,21 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
+// Installed neural operator: FP32 master parameters, gradient, Adam moments.
+struct NoState {
+    bool loaded = false;
+    nop_no_config cfg{};
+    long long n_params = 0;
+    float* params = nullptr;
+    float* grad = nullptr;
+    float* adam_m = nullptr;
+    float* adam_v = nullptr;
+    int adam_t = 0;
+    // offsets of every tensor in the flat parameter array
+    std::vector<long long> off;
+    std::vector<long long> len;
+};
+
 // Problem state of a 1D slab batch (device side unless noted).
 struct SlabDev {
     int n_inst = 0;
@@ -44,6 +59,7 @@ struct SlabDev {
     int* ncell_d = nullptr;
     int* nang_d = nullptr;
     double* dx_d = nullptr;
+    double* width_d = nullptr;
     int* qoff_d = nullptr;           // offset of the instance's nodes in mu_d/w_d
     long long* boff_d = nullptr;     // offset of the instance's boundary fluxes
     long long bnd_total = 0;
@@ -78,6 +94,7 @@ struct nop_ctx {
     nop::SlabDev slab;
     nop::XYDev xy;
     long long C = 0;
+    nop::NoState no;
     // FP64 originals
     double *sigt_d = nullptr, *sigs_d = nullptr, *src_d = nullptr, *nsf_d = nullptr,
            *chi_d = nullptr;
@@ -122,6 +139,17 @@ int build_level_symmetric_s8(nop_ctx* ctx);
 int sn1d_solve(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* phi0,
                bool phi0_dev, const double* k0, double* phi_out, bool out_dev,
                double* k_out, nop_stats* st);
+
+// Neural operators (deeponet.cu, fno.cu)
+int no_layout(const nop_no_config* cfg, std::vector<long long>* off,
+              std::vector<long long>* len, long long* total);
+int deeponet_forward_raw(nop_ctx* ctx, int n, const float* U, int P, const float* X,
+                         float* out, bool keep);
+int deeponet_backward(nop_ctx* ctx, int n, int P, const float* dout, const float* U,
+                      const float* X);
+int deeponet_project(nop_ctx* ctx, const double* field_host, float* out_host);
+int deeponet_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* status_d,
+                    int* iters_d, bool predict_only, const double* src_d);
 
 // Lane split of the 1D sweep (log2 lanes per angle group, angles per lane).
 void sn1d_pick_config(int cells, int order, int* lg_ng, int* A);

@@ -1,0 +1,35 @@
+"""Training data and training runs for the neural operator, through the C ABI.
+
+The operator is trained once at p* on solutions the solver itself produces
+(Sec. 5.1: a single constant cross-section pair; App. A1: GRF sources of unit
+integral, MSE loss, Adam).  Every step here is a library call: the batch of
+p* problems is solved by nop_solve_fixed_source, the branch inputs come from
+the operator's input map nop_no_sensors, and the optimisation runs in
+nop_no_train.  The random sources and the sample order are inputs.
+"""
+import numpy as np
+
+
+def deeponet_training_set(solver, cfg, sources, order=32, tol=1e-7, itmax=100000):
+    """Solve the p* problem for every source row (n x I cells over cfg.length).
+
+    Returns (branch inputs [n, sensors], trunk coordinates [I], targets [n, I]).
+    The operator `cfg` must be installed (its sensor count defines the input map).
+    """
+    n, I = sources.shape
+    st, ss = cfg.sigma_t_star, cfg.sigma_s_star
+    solver.set_slabs(np.full(n, I), np.full(n, cfg.length), np.full(n, order),
+                     np.full(n * I, st), np.full(n * I, ss), source=sources.reshape(-1))
+    phi, info = solver.solve_fixed_source(tol=tol, itmax=itmax, precision=0)
+    U = solver.no_sensors(sources.reshape(-1))
+    X = (np.arange(I) + 0.5) / I
+    return U, X, phi.reshape(n, I), info
+
+
+def train(solver, U, X, Y, steps, batch, seed, lr=1e-3):
+    """Adam on (U, X, Y) with a seeded sample order; returns the loss history."""
+    rng = np.random.default_rng(seed)
+    n = U.shape[0]
+    order = np.concatenate([rng.permutation(n) for _ in range((steps * batch) // n + 1)])
+    return solver.no_train(U, Y, X, steps=steps, batch=batch, lr=lr,
+                           order=order[:steps * batch])
