@@ -261,6 +261,12 @@ int nop_set_problem(nop_ctx* ctx, const nop_problem* p) {
     if (p->geometry == NOP_GEOM_SLAB) {
         nop::SlabDev& s = ctx->slab;
         const int B = p->n_inst;
+        // the schedule cache survives a new problem with the same batch layout
+        const bool same_layout = s.n_inst == B &&
+                                 std::equal(s.ncell.begin(), s.ncell.end(), p->n_cells) &&
+                                 std::equal(s.order.begin(), s.order.end(), p->order) &&
+                                 (int)s.last_iters.size() == B;
+        if (!same_layout) s.last_iters.assign(B, 0);
         s.n_inst = B;
         s.C = C;
         s.ncell.assign(p->n_cells, p->n_cells + B);

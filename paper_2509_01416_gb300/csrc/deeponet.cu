@@ -20,6 +20,8 @@
 #include <cstdio>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "nn_kernels.cuh"
 
 namespace nop {
@@ -345,6 +347,141 @@ __global__ void trunk_dot_kernel(long long c0, int n, int p, const float* Tn, co
     if (lane == 0) phi[c0 + k] = acc;
 }
 
+// ---- fused trunk evaluation at cell centres (width = basis = 128, depth 4)
+// One persistent block of 8 warps holds the three 128 x 128 trunk matrices as
+// BF16 in shared memory; each warp owns 16 points of a 128-point tile and runs
+// layer 1 (elementwise, K = 1), layers 2-4 on mma.sync (BF16 operands, FP32
+// accumulation, activations rounded to BF16 between layers like the generic
+// GEMM), then the inner product with its instance's coefficients.
+constexpr int FT_W = 128, FT_PAD = 8, FT_WARPS = 8, FT_PTS = 16 * FT_WARPS;
+
+__device__ __forceinline__ void ft_mma(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
+                                       uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(32 * FT_WARPS) trunk_fused_kernel(
+    long long C, int B, const long long* cell_off, const int* ncell, const float* W1,
+    const float* b1, const float* W2, const float* b2, const float* W3, const float* b3,
+    const float* W4, const float* b4, const float* beta_keep, const int* status, double* phi) {
+    extern __shared__ __align__(16) unsigned char ft_smem[];
+    __nv_bfloat16(*Ws)[FT_W][FT_W + FT_PAD] = (__nv_bfloat16(*)[FT_W][FT_W + FT_PAD])ft_smem;
+    __nv_bfloat16(*H)[FT_W + FT_PAD] =
+        (__nv_bfloat16(*)[FT_W + FT_PAD])(ft_smem + 3 * sizeof(__nv_bfloat16) * FT_W * (FT_W + FT_PAD));
+    __shared__ float bs[4][FT_W], w1s[FT_W];
+    __shared__ int pinst[FT_PTS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int gq = lane >> 2, tq = lane & 3;
+    for (int e = tid; e < FT_W * FT_W; e += blockDim.x) {
+        const int n = e / FT_W, k = e % FT_W;
+        Ws[0][n][k] = __float2bfloat16_rn(W2[e]);
+        Ws[1][n][k] = __float2bfloat16_rn(W3[e]);
+        Ws[2][n][k] = __float2bfloat16_rn(W4[e]);
+    }
+    for (int n = tid; n < FT_W; n += blockDim.x) {
+        w1s[n] = W1[n];
+        bs[0][n] = b1[n];
+        bs[1][n] = b2[n];
+        bs[2][n] = b3[n];
+        bs[3][n] = b4[n];
+    }
+    __syncthreads();
+    for (long long t0 = (long long)blockIdx.x * FT_PTS; t0 < C; t0 += (long long)gridDim.x * FT_PTS) {
+        // owning instance and coordinate of the warp's 16 points, one lane each
+        const int r0 = warp * 16;
+        float xl = 0.f;
+        if (lane < 16) {
+            const long long c = t0 + r0 + lane;
+            int b = -1;
+            if (c < C) {
+                int lo = 0, hi = B - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (cell_off[mid] <= c) lo = mid;
+                    else hi = mid - 1;
+                }
+                b = lo;
+                xl = (float)((c - cell_off[lo] + 0.5) / ncell[lo]);
+            }
+            pinst[r0 + lane] = b;
+        }
+        // layer 1 for the warp's 16 points: h = relu(x w1 + b1), BF16
+        for (int rr = 0; rr < 16; ++rr) {
+            const float x = __shfl_sync(0xffffffffu, xl, rr);
+            // the trunk input is rounded to BF16 like any GEMM operand
+            const float xb = __bfloat162float(__float2bfloat16_rn(x));
+            for (int n = lane; n < FT_W; n += 32) {
+                const float w = __bfloat162float(__float2bfloat16_rn(w1s[n]));
+                H[r0 + rr][n] = __float2bfloat16_rn(fmaxf(xb * w + bs[0][n], 0.f));
+            }
+        }
+        __syncwarp();
+        float acc[16][4];
+        for (int l = 0; l < 3; ++l) {
+#pragma unroll
+            for (int nt = 0; nt < 16; ++nt)
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) acc[nt][c4] = 0.f;
+#pragma unroll
+            for (int kk = 0; kk < FT_W; kk += 16) {
+                uint32_t af[4];
+                af[0] = *(const uint32_t*)&H[r0 + gq][kk + 2 * tq];
+                af[1] = *(const uint32_t*)&H[r0 + gq + 8][kk + 2 * tq];
+                af[2] = *(const uint32_t*)&H[r0 + gq][kk + 2 * tq + 8];
+                af[3] = *(const uint32_t*)&H[r0 + gq + 8][kk + 2 * tq + 8];
+#pragma unroll
+                for (int nt = 0; nt < 16; ++nt) {
+                    const int n = nt * 8 + gq;
+                    const uint32_t b0 = *(const uint32_t*)&Ws[l][n][kk + 2 * tq];
+                    const uint32_t b1v = *(const uint32_t*)&Ws[l][n][kk + 2 * tq + 8];
+                    ft_mma(acc[nt], af, b0, b1v);
+                }
+            }
+            __syncwarp();
+            if (l < 2) {
+#pragma unroll
+                for (int nt = 0; nt < 16; ++nt)
+#pragma unroll
+                    for (int h2 = 0; h2 < 2; ++h2)
+#pragma unroll
+                        for (int cc = 0; cc < 2; ++cc) {
+                            const int n = nt * 8 + 2 * tq + cc;
+                            H[r0 + gq + 8 * h2][n] =
+                                __float2bfloat16_rn(fmaxf(acc[nt][2 * h2 + cc] + bs[l + 1][n], 0.f));
+                        }
+                __syncwarp();
+            }
+        }
+        // output layer values + bias, inner product with the instance's beta
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+            const int row = r0 + gq + 8 * h2;
+            const int b = pinst[row];
+            float d = 0.f;
+            if (b >= 0 && (!status || status[b] != 3)) {
+#pragma unroll
+                for (int nt = 0; nt < 16; ++nt)
+#pragma unroll
+                    for (int cc = 0; cc < 2; ++cc) {
+                        const int n = nt * 8 + 2 * tq + cc;
+                        const float tv = acc[nt][2 * h2 + cc] + bs[3][n];
+                        d += __bfloat162float(__float2bfloat16_rn(tv)) *
+                             __bfloat162float(__float2bfloat16_rn(beta_keep[(long long)b * FT_W + n]));
+                    }
+            }
+            d += __shfl_xor_sync(0xffffffffu, d, 1);
+            d += __shfl_xor_sync(0xffffffffu, d, 2);
+            const long long c = t0 + row;
+            if (tq == 0 && c < C) phi[c] = d;
+        }
+        __syncwarp();
+    }
+}
+
 __global__ void bin_centres_kernel(int M, float* X) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m < M) X[m] = (float)((m + 0.5) / M);
@@ -536,6 +673,9 @@ int deeponet_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* sta
                                                         run, active);
         if (cudaGetLastError() != cudaSuccess) { rc = NOP_ECUDA; break; }
         ctx->count_launch(false);
+        // converged instances are frozen, so the host checks for completion
+        // only every few iterations
+        if (it % 4 != 0 && it != imax) continue;
         if (cudaMemcpyAsync(active_h, active, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream) !=
                 cudaSuccess ||
             cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
@@ -549,8 +689,31 @@ int deeponet_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* sta
         ctx->set_error("recast iteration failed");
         return rc;
     }
-    // final flux at every cell centre, in chunks of points
+    // final flux at every cell centre
     const long long C = s.C;
+    if (c.width == FT_W && c.basis == FT_W && c.depth == 4) {
+        const size_t smem = 3 * sizeof(__nv_bfloat16) * FT_W * (FT_W + FT_PAD) +
+                            sizeof(__nv_bfloat16) * FT_PTS * (FT_W + FT_PAD);
+        NOP_CUDA_TRY(ctx, cudaFuncSetAttribute(trunk_fused_kernel,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem));
+        const int grid = (int)std::max<long long>(
+            1, std::min<long long>((C + FT_PTS - 1) / FT_PTS, ctx->sm_count));
+        trunk_fused_kernel<<<grid, 32 * FT_WARPS, smem, ctx->stream>>>(
+            C, B, s.cell_off_d, s.ncell_d, Wp(ctx, 1, 0), Bp(ctx, 1, 0), Wp(ctx, 1, 1),
+            Bp(ctx, 1, 1), Wp(ctx, 1, 2), Bp(ctx, 1, 2), Wp(ctx, 1, 3), Bp(ctx, 1, 3), beta_keep,
+            status, phi_d);
+        NOP_CUDA_TRY(ctx, cudaGetLastError());
+        ctx->count_launch(false);
+        ctx->phase_end(mk);
+        if (status_d)
+            NOP_CUDA_TRY(ctx, cudaMemcpyAsync(status_d, status, sizeof(int) * B,
+                                              cudaMemcpyDeviceToDevice, ctx->stream));
+        if (iters_d)
+            NOP_CUDA_TRY(ctx, cudaMemcpyAsync(iters_d, iters, sizeof(int) * B,
+                                              cudaMemcpyDeviceToDevice, ctx->stream));
+        return NOP_OK;
+    }
     const int CH = 1 << 16;
     NOP_TRY(ctx->scratch("rc_Xc", sizeof(float) * CH, &q));
     float* Xc = (float*)q;

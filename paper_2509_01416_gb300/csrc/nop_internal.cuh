@@ -54,6 +54,8 @@ struct SlabDev {
     std::vector<int> ncell, order;   // host copies
     std::vector<double> width;
     std::vector<double> cmax;        // host: largest in-group scattering ratio
+    std::vector<int> last_iters;     // host: iterations of each instance in the last solve
+                                     // of this batch layout (0 = unknown); the scheduler's cost
     std::vector<long long> cell_off; // host prefix sums
     long long* cell_off_d = nullptr;
     int* ncell_d = nullptr;

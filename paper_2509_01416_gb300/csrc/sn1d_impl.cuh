@@ -27,9 +27,9 @@
 #pragma once
 #include "nop_internal.cuh"
 
-#define SN1D_THREADS 256
+#define SN1D_THREADS 128
 #define SN1D_BLOCKS_PER_SM 3
-#define SN1D_SMEM_BYTES (72 * 1024)
+#define SN1D_STAGE_BYTES (64 * 1024)
 
 namespace nop {
 
@@ -123,13 +123,16 @@ struct Grp {
     }
 };
 
-// Shared-memory staging of the block path: the source of every cell and one
-// row of partial angle sums per warp (each warp owns its row, so the sweeps
-// need no atomics; the rows are added after the sweep).
+// Shared-memory staging of an instance: {sigma_t, s} of every cell, read by
+// every sweep step, so the steps never wait on global memory.  The warp path
+// stages into the warp's own slab of the block's shared memory (instances up
+// to `cells`; larger ones read global memory); the block path stages once per
+// block and adds one row of partial angle sums per warp (each warp owns its
+// row, so the sweeps need no atomics; the rows are added after the sweep).
 template <typename T>
 struct Stage {
-    T* s;
-    T* part;      // [nwarps][cells]
+    Cell2<T>* ss;   // [cells] or null (unstaged)
+    T* part;        // block path: [nwarps][cells]
     int cells;
 };
 
@@ -167,14 +170,16 @@ struct CSum {
 // maps over the chunks, then sweep.  The angle sum of a cell is reduced over
 // the ng lanes of its chunk with xor shuffles; lane (k mod ng) owns the k-th
 // cell of the chunk.  Warp path: the owner stores the MINUS partial sum in U
-// and completes the cell in the PLUS half.  Block path: the source comes from
-// shared memory and owners add their partial sums there.
+// and completes the cell in the PLUS half, accumulating the squared change
+// and the squared flux (FP32 per lane within one iteration: the change of an
+// FP32 flux is exact, and the FP64 sum across lanes forms the norms).  Block
+// path: owners add their partial sums to the warp's row.
 template <typename T, int A, bool MINUS>
 __device__ __forceinline__ void sweep_half(const bool block, Cell4<T>* X, Cell2<T>* U,
                                            const Stage<T>& sg, int I, int lg,
                                            const T (&cc)[A], const T (&wt)[A],
                                            const T (&psi_bnd)[A], T (&psi_out)[A],
-                                           double& acc_d, double& acc_n) {
+                                           T& acc_d, T& acc_n) {
     const int lane = threadIdx.x & 31;
     const int ng = 1 << lg, nt = 32 >> lg;
     const int j = lane & (ng - 1), t = lane >> lg;
@@ -195,9 +200,10 @@ __device__ __forceinline__ void sweep_half(const bool block, Cell4<T>* X, Cell2<
         for (int k = 0; k < len; ++k) {
             const int i = MINUS ? (I - 1 - (k0 + k)) : (k0 + k);
             T st, s;
-            if (block) {
-                st = X[i].st;
-                s = sg.s[i];
+            if (sg.ss) {
+                const Cell2<T> w2 = sg.ss[i];
+                st = w2.s0;
+                s = w2.s1;
             } else {
                 const Cell4<T> v = X[i];
                 st = v.st;
@@ -243,17 +249,24 @@ __device__ __forceinline__ void sweep_half(const bool block, Cell4<T>* X, Cell2<
     for (int k = 0; k < m; ++k) {
         const bool valid = k < len;
         const int i = MINUS ? (I - 1 - (k0 + k)) : (k0 + k);
-        T p = T(0), s = T(0), phio = T(0);
+        T p = T(0), s = T(0), phio = T(0), pmv = T(0);
         if (valid) {
             T st;
-            if (block) {
-                st = X[i].st;
-                s = sg.s[i];
+            if (sg.ss) {
+                const Cell2<T> w2 = sg.ss[i];
+                st = w2.s0;
+                s = w2.s1;
+                if (!block && !MINUS) {
+                    // the owner's operands, fetched early
+                    phio = X[i].phi;
+                    pmv = U[i].s1;
+                }
             } else {
                 const Cell4<T> v = X[i];
                 st = v.st;
                 phio = v.phi;
                 s = MINUS ? (v.y * v.phi + v.z) : U[i].s0;
+                if (!MINUS) pmv = U[i].s1;
             }
 #pragma unroll
             for (int q = 0; q < A; ++q) {
@@ -272,10 +285,10 @@ __device__ __forceinline__ void sweep_half(const bool block, Cell4<T>* X, Cell2<
                 u.s1 = p;
                 U[i] = u;
             } else {
-                const T phin = p + U[i].s1;
-                const double df = (double)phin - (double)phio;
+                const T phin = p + pmv;
+                const T df = phin - phio;
                 acc_d += df * df;
-                acc_n += (double)phin * (double)phin;
+                acc_n += phin * phin;
                 X[i].phi = phin;
             }
         }
@@ -310,7 +323,7 @@ __device__ double si_iteration(const Sn1dArgs& a, const Grp& gr, const Stage<T>&
     const int lane = threadIdx.x & 31;
     const int j = lane & ((1 << lg) - 1);
     T* PB = (T*)a.psib + a.boff[inst];
-    double acc_d = 0.0, acc_n = 0.0;
+    T acc_d = T(0), acc_n = T(0);
     for (int g = 0; g < a.G; ++g) {
         if (a.G > 1) {
             group_source<T>(a, gr, off, I, g);
@@ -318,11 +331,15 @@ __device__ double si_iteration(const Sn1dArgs& a, const Grp& gr, const Stage<T>&
         }
         Cell4<T>* X = (Cell4<T>*)a.X + (long long)g * a.C + off;
         Cell2<T>* U = (Cell2<T>*)a.U + off;
-        if (gr.block) {
+        if (sg.ss) {
             for (int i = gr.rank; i < I; i += gr.size) {
                 const Cell4<T> v = X[i];
-                sg.s[i] = v.y * v.phi + v.z;
-                for (int w = 0; w < gr.nwarps; ++w) sg.part[w * sg.cells + i] = T(0);
+                Cell2<T> w2;
+                w2.s0 = v.st;
+                w2.s1 = v.y * v.phi + v.z;
+                sg.ss[i] = w2;
+                if (gr.block)
+                    for (int w = 0; w < gr.nwarps; ++w) sg.part[w * sg.cells + i] = T(0);
             }
             gr.sync();
         }
@@ -352,17 +369,17 @@ __device__ double si_iteration(const Sn1dArgs& a, const Grp& gr, const Stage<T>&
             for (int i = gr.rank; i < I; i += gr.size) {
                 T phin = T(0);
                 for (int w = 0; w < gr.nwarps; ++w) phin += sg.part[w * sg.cells + i];
-                const double df = (double)phin - (double)X[i].phi;
+                const T df = phin - X[i].phi;
                 acc_d += df * df;
-                acc_n += (double)phin * (double)phin;
+                acc_n += phin * phin;
                 X[i].phi = phin;
             }
             gr.sync();
         }
     }
-    acc_d = gr.sum(acc_d);
-    acc_n = gr.sum(acc_n);
-    return acc_n > 0.0 ? sqrt(acc_d / acc_n) : (acc_d > 0.0 ? INFINITY : 0.0);
+    const double sd = gr.sum((double)acc_d);
+    const double sn = gr.sum((double)acc_n);
+    return sn > 0.0 ? sqrt(sd / sn) : (sd > 0.0 ? INFINITY : 0.0);
 }
 
 // production integral sum nsf * phi * dx over the instance (FP64)
@@ -547,12 +564,13 @@ __global__ void __launch_bounds__(SN1D_THREADS, SN1D_BLOCKS_PER_SM) sn1d_kernel(
     __shared__ double red[SN1D_THREADS / 32];
     __shared__ int job;
     const int lane = threadIdx.x & 31;
-    T* smem = (T*)smem_raw;
-    Stage<T> sg;
-    sg.s = smem;
-    sg.part = smem + a.smem_cells;
-    sg.cells = a.smem_cells;
+    constexpr int nw = SN1D_THREADS / 32;
     if (a.n_big > 0) {
+        // block path: [cells] staged pairs, then nw rows of partial sums
+        Stage<T> sg;
+        sg.ss = (Cell2<T>*)smem_raw;
+        sg.cells = a.smem_cells;
+        sg.part = (T*)(sg.ss + a.smem_cells);
         Grp gb;
         gb.block = true;
         gb.rank = threadIdx.x;
@@ -568,7 +586,10 @@ __global__ void __launch_bounds__(SN1D_THREADS, SN1D_BLOCKS_PER_SM) sn1d_kernel(
             if (jb >= a.n_big) break;
             dispatch<T>(a, gb, sg, a.big_list[jb]);
         }
+        __syncthreads();
     }
+    // warp path: each warp stages into its own slab
+    constexpr int slab = SN1D_STAGE_BYTES / (nw * (int)sizeof(Cell2<T>));
     Grp gw;
     gw.block = false;
     gw.rank = lane;
@@ -581,7 +602,14 @@ __global__ void __launch_bounds__(SN1D_THREADS, SN1D_BLOCKS_PER_SM) sn1d_kernel(
         if (lane == 0) jw = atomicAdd(a.counter, 1);
         jw = __shfl_sync(0xffffffffu, jw, 0);
         if (jw >= a.n_small) return;
-        dispatch<T>(a, gw, sg, a.order_list[jw]);
+        const int inst = a.order_list[jw];
+        Stage<T> sw;
+        sw.ss = a.ncell[inst] <= slab
+                    ? (Cell2<T>*)smem_raw + (threadIdx.x >> 5) * slab
+                    : nullptr;
+        sw.part = nullptr;
+        sw.cells = slab;
+        dispatch<T>(a, gw, sw, inst);
     }
 }
 
@@ -662,44 +690,61 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
     }
 
     // ---- scheduling (host side).  Estimated work of an instance: cells x
-    // angles x iterations, the iterations from the largest in-group
-    // scattering ratio c (source iteration contracts roughly like c).  The
-    // persistent grid has `warps_total` warps; an instance worth more than
-    // eight times a warp's fair share of the batch runs on a whole block (its angles
-    // split over the block's warps) so that it does not set the critical path.
+    // angles x iterations; the iterations are those of the previous solve of
+    // the same batch layout when known, else estimated from the largest
+    // in-group scattering ratio c (source iteration contracts roughly like c).
     const int blocks_max = ctx->sm_count * SN1D_BLOCKS_PER_SM;
     const double tol_its = eigen ? std::min(o->tol_inner, o->tol) : o->tol;
     std::vector<double> cost(B);
     double total_cost = 0;
     for (int b = 0; b < B; ++b) {
         const double c = std::min(0.999, std::max(0.2, s.cmax[b]));
-        const double its = std::min(5000.0, std::max(5.0, std::log(tol_its) / std::log(c)));
+        double its = std::min(5000.0, std::max(5.0, std::log(tol_its) / std::log(c)));
+        if (!eigen && b < (int)s.last_iters.size() && s.last_iters[b] > 0) its = s.last_iters[b];
         cost[b] = (double)s.ncell[b] * s.order[b] * its * G;
         total_cost += cost[b];
     }
-    const int max_smem_cells = (int)(SN1D_SMEM_BYTES / ((1 + SN1D_THREADS / 32) * sizeof(T)));
+    const int max_smem_cells =
+        (int)(SN1D_STAGE_BYTES / (sizeof(Cell2<T>) + (SN1D_THREADS / 32) * sizeof(T)));
     const int warps_total =
         (int)std::max<long long>(1, std::min<long long>(B, (long long)blocks_max * (SN1D_THREADS / 32)));
-    const double share = total_cost / warps_total;
+    // Latency of an instance on one warp: iterations x sequential cell steps
+    // per iteration of its lane split (4 passes of ceil(I/nt) steps when the
+    // cells are chunked, 2 otherwise).  With longest-first scheduling the
+    // batch takes about max(mean warp load, longest latency); an instance
+    // whose latency is well above the mean warp load runs on a whole block,
+    // which cuts its latency at the price of the block's other warps.
     std::vector<int> cfg(B), small, big;
+    std::vector<double> lat(B);
+    double lat_sum = 0;
+    for (int b = 0; b < B; ++b) {
+        int lg, A;
+        sn1d_pick_config(s.ncell[b], s.order[b], &lg, &A);
+        cfg[b] = (lg << 8) | A;
+        const int nt = 32 >> lg;
+        const double steps = (nt > 1 ? 4.0 : 2.0) * ((s.ncell[b] + nt - 1) / nt) * G;
+        lat[b] = cost[b] / ((double)s.ncell[b] * s.order[b] * G) * steps;
+        lat_sum += lat[b];
+    }
+    const double mean_load = lat_sum / warps_total;
     int smem_cells = 1;
     for (int b = 0; b < B; ++b) {
         const int h = s.order[b] / 2;
         const bool fits = h >= SN1D_THREADS / 32 && s.ncell[b] <= max_smem_cells;
         const bool is_big =
             fits && (o->schedule == NOP_SCHED_BLOCK ||
-                     (o->schedule == NOP_SCHED_AUTO && B > 1 && cost[b] > 8.0 * share));
-        int lg, A;
+                     (o->schedule == NOP_SCHED_AUTO && B > 1 && lat[b] > 1.5 * mean_load));
         if (is_big) {
+            int lg, A;
             const int hw = (h + SN1D_THREADS / 32 - 1) / (SN1D_THREADS / 32);
             sn1d_pick_config(s.ncell[b], 2 * hw, &lg, &A);
+            cfg[b] = (lg << 8) | A;
             big.push_back(b);
             smem_cells = std::max(smem_cells, s.ncell[b]);
         } else {
-            sn1d_pick_config(s.ncell[b], s.order[b], &lg, &A);
             small.push_back(b);
         }
-        cfg[b] = (lg << 8) | A;
+        cost[b] = lat[b];
     }
     auto longest_first = [&](int x, int y) { return cost[x] > cost[y]; };
     std::stable_sort(small.begin(), small.end(), longest_first);
@@ -775,10 +820,10 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
         1, std::min<long long>(blocks_max, (long long)big.size() +
                                                ((long long)small.size() + SN1D_THREADS / 32 - 1) /
                                                    (SN1D_THREADS / 32)));
-    const size_t smem = (1 + SN1D_THREADS / 32) * sizeof(T) * (size_t)smem_cells;
+    const size_t smem = SN1D_STAGE_BYTES;
     NOP_CUDA_TRY(ctx, cudaFuncSetAttribute(sn1d_kernel<T>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)SN1D_SMEM_BYTES));
+                                           (int)SN1D_STAGE_BYTES));
     mk = ctx->phase_begin(0);
     sn1d_kernel<T><<<blocks, SN1D_THREADS, smem, ctx->stream>>>(a);
     NOP_CUDA_TRY(ctx, cudaGetLastError());
@@ -847,6 +892,8 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
         st->max_outer = 0;
         st->max_change = 0;
     }
+    if (!eigen && (int)s.last_iters.size() == B)
+        for (int b = 0; b < B; ++b) s.last_iters[b] = it_h[b];
     for (int b = 0; b < B; ++b) {
         if (ctx->timing)
             ctx->cell_angle_updates += (double)it_h[b] * s.ncell[b] * s.order[b] * G;

@@ -108,9 +108,11 @@ def _setup_instances(solver, Is, seed=0):
     return insts
 
 
-def test_predict_matches_oracle(solver):
+@pytest.mark.parametrize("width,p", [(64, 32), (128, 128)])
+def test_predict_matches_oracle(solver, width, p):
+    # 128 x 128 x depth 4 takes the fused trunk kernel, other shapes the GEMM chain
     insts = _setup_instances(solver, [100, 256, 77])
-    cfg, P = _small(solver, m=128, width=64, p=32, seed=9)
+    cfg, P = _small(solver, m=128, width=width, p=p, seed=9)
     rng = np.random.default_rng(8)
     srcs = [rng.uniform(-0.5, 1.0, s.I) for s in insts]
     got = split(solver.no_predict(np.concatenate(srcs)), insts)
