@@ -302,6 +302,36 @@ int nop_no_predict(nop_ctx *ctx, const double *src, double *phi_out);
 int nop_recast_iterate(nop_ctx *ctx, double tol, int itmax, int flags, double *phi_out,
                        nop_stats *stats);
 
+/* --------------------------------------------------- allocation-free solve */
+
+#define NOP_NOALLOC_MAX_CELLS  65536
+#define NOP_NOALLOC_MAX_ORDER  128
+
+/* Solve one single-group fixed-source slab (vacuum faces, zero initial flux,
+ * FP32 sweeps with FP64 norms, Gauss-Legendre S_N) without allocating any
+ * memory.  For callers that cannot call cudaMalloc -- code that runs while a
+ * stream is captured into a graph, or hosts that forbid device allocations
+ * outside a reserved budget.  The paper has no counterpart; this is a library
+ * convenience.
+ *
+ * All pointers are device pointers: sigma_t, sigma_s (in-group scattering),
+ * source (the isotropic S of Eq. 12) are [n_cells] doubles on equal cells
+ * over [0, width]; phi_out receives the [n_cells] scalar flux; stats_out
+ * receives {source iterations, status (0 or NOP_ENOCONV / NOP_ENAN)}.  Work
+ * is enqueued on `stream` (a cudaStream_t, NULL = legacy default stream) and
+ * the call returns without synchronising.
+ *
+ * Limits: n_cells <= NOP_NOALLOC_MAX_CELLS, even order <= NOP_NOALLOC_MAX_ORDER;
+ * anything larger returns NOP_EINVAL.  The scratch is one fixed device array
+ * of about 1.8 MB that every GPU loading the library holds until exit; calls
+ * that overlap on the GPU race on it and must be serialised by the caller.
+ * The first call on a device (with that device current) looks up the array's
+ * address; make it before any stream capture. */
+int nop_slab_solve_noalloc(const double *sigma_t, const double *sigma_s,
+                           const double *source, int n_cells, double width, int order,
+                           double tol, int itmax, double *phi_out, int *stats_out,
+                           void *stream);
+
 /* --------------------------------------------------------------- tracing */
 
 /* Device-side phase times accumulated since timing was enabled. */

@@ -20,6 +20,7 @@ NOP_PREC_F32, NOP_PREC_F64 = 0, 1
 NOP_WARM_NONE, NOP_WARM_RECAST = 0, 1
 NOP_PHI0_DEVICE, NOP_OUT_DEVICE = 1, 2
 NOP_SCHED_AUTO, NOP_SCHED_WARP, NOP_SCHED_BLOCK = 0, 1, 2
+NOP_NOALLOC_MAX_CELLS, NOP_NOALLOC_MAX_ORDER = 65536, 128
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
@@ -86,6 +87,9 @@ SIGNATURES = {
     "nop_solve_fixed_source": (C.c_int, [C.c_void_p, C.POINTER(nop_solve_opts), C.c_void_p,
                                          C.c_void_p, C.POINTER(nop_stats)]),
     "nop_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "nop_slab_solve_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
+                                         C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
+                                         C.c_void_p]),
     "nop_no_param_count": (C.c_int, [C.POINTER(nop_no_config), C.POINTER(C.c_longlong)]),
     "nop_no_set": (C.c_int, [C.c_void_p, C.POINTER(nop_no_config), _fp]),
     "nop_no_get": (C.c_int, [C.c_void_p, _fp]),

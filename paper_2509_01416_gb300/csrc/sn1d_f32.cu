@@ -5,3 +5,22 @@ namespace nop {
 template int sn1d_run<float>(nop_ctx*, const nop_solve_opts*, bool, const double*, const double*,
                           double*, bool, double*, nop_stats*);
 }  // namespace nop
+
+namespace nop {
+// Launch sequence of one single-group slab solve whose every buffer the
+// caller supplies (used by the allocation-free entry point): preparation,
+// the persistent solve kernel on one block, conversion of the flux.
+int sn1d_launch_f32(const Sn1dArgs& a, long long C, const double* sigt, const double* sigs,
+                    const double* src, Cell4<float>* X, float* ext, double* phi_out,
+                    cudaStream_t stream) {
+    if (cudaFuncSetAttribute(sn1d_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SN1D_STAGE_BYTES) != cudaSuccess)
+        return NOP_ECUDA;
+    const int pb = (int)std::max<long long>(1, std::min<long long>((C + 255) / 256, 1024));
+    sn1d_prepare<float><<<pb, 256, 0, stream>>>(C, 1, sigt, sigs, src, nullptr, nullptr, 0, X,
+                                                nullptr, ext, nullptr);
+    sn1d_kernel<float><<<1, SN1D_THREADS, SN1D_STAGE_BYTES, stream>>>(a);
+    sn1d_finish<float><<<pb, 256, 0, stream>>>(C, X, phi_out);
+    return cudaGetLastError() == cudaSuccess ? NOP_OK : NOP_ECUDA;
+}
+}  // namespace nop
