@@ -278,10 +278,10 @@ def power_iteration(prob, quad, tol_k=1e-10, tol_phi=1e-10, tol_inner=1e-10,
     n = 0
     for n in range(1, itmax_outer + 1):
         F = np.sum(prob.nusigf * phi, axis=0)
-        src = prob.chi[:, None] * F[None] / k if prob.chi.ndim == 1 else None
-        if src is None:
+        if prob.chi.ndim != 1:
             raise ValueError("chi must be a (G,) vector")
-        src = src.reshape(prob.sigt.shape)
+        # chi_g F / k for every group, F the production density of each cell
+        src = prob.chi.reshape((G,) + (1,) * F.ndim) * F[None] / k
         r = source_iteration(prob, quad, src=src, phi0=phi, tol=tol_inner,
                              itmax=itmax_inner, sweeper=sw)
         inner_total += r.iterations

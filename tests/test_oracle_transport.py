@@ -393,5 +393,32 @@ def test_2d_matches_dense_dd_system():
     assert np.max(np.abs(r.phi[0] - phi)) < 1e-11 * np.max(phi)
 
 
+def test_2d_reflective_homogeneous_k():
+    # all faces reflective, uniform data: k = nu Sigma_f / Sigma_a exactly
+    n = 5
+    bc = {f: T.REFLECTIVE for f in ("x0", "xL", "y0", "yL")}
+    P = T.XY(dx=0.4, dy=0.6, sigt=np.full((1, n, n), 1.1), sigs=np.full((1, 1, n, n), 0.6),
+             nusigf=np.full((1, n, n), 0.55), chi=np.ones(1), bc=bc)
+    e = T.power_iteration(P, Qd.level_symmetric_s8(), tol_k=1e-13, tol_phi=1e-11,
+                          tol_inner=1e-13)
+    assert abs(e.k - 0.55 / 0.5) < 1e-10
+
+
+def test_2d_multigroup_infinite_medium_k():
+    g = _golden("table10_multigroup_k.txt")
+    S = np.stack([g["sigma_s_row_from_g1"], g["sigma_s_row_from_g2"],
+                  g["sigma_s_row_from_g3"]])
+    st, nsf, chi = g["sigma_t"], g["nu"] * g["sigma_f"], g["chi"]
+    kinf = max(np.linalg.eigvals(np.linalg.solve(np.diag(st) - S.T, np.outer(chi, nsf))).real)
+    n = 4
+    bc = {f: T.REFLECTIVE for f in ("x0", "xL", "y0", "yL")}
+    one = np.ones((n, n))
+    P = T.XY(dx=0.5, dy=0.5, sigt=st[:, None, None] * one, sigs=S[:, :, None, None] * one,
+             nusigf=nsf[:, None, None] * one, chi=chi, bc=bc)
+    e = T.power_iteration(P, Qd.level_symmetric_s8(), tol_k=1e-13, tol_phi=1e-11,
+                          tol_inner=1e-13)
+    assert abs(e.k - kinf) < 1e-9
+
+
 def test_native_sweep_loads():
     assert os.path.exists(native.build())
