@@ -396,8 +396,10 @@ int nop_solve_fixed_source(nop_ctx* ctx, const nop_solve_opts* o, const double* 
     if (ctx->geometry == NOP_GEOM_SLAB)
         return nop::sn1d_solve(ctx, o, false, phi0, phi0_dev, nullptr, phi_out,
                                (o->flags & NOP_OUT_DEVICE) != 0, nullptr, st);
-    ctx->set_error("x-y solver not available");
-    return NOP_EINVAL;
+    nop_solve_opts o2 = *o;
+    if (phi0_dev) o2.flags |= NOP_PHI0_DEVICE;
+    return nop::xy_solve(ctx, &o2, false, phi0, 0.0, phi_out, (o->flags & NOP_OUT_DEVICE) != 0,
+                         nullptr, st);
 }
 
 int nop_solve_eigen(nop_ctx* ctx, const nop_solve_opts* o, const double* phi0, double k0,
@@ -423,8 +425,8 @@ int nop_solve_eigen(nop_ctx* ctx, const nop_solve_opts* o, const double* phi0, d
                                k0v.data(), phi_out, (o->flags & NOP_OUT_DEVICE) != 0, k_out,
                                st);
     }
-    ctx->set_error("x-y solver not available");
-    return NOP_EINVAL;
+    return nop::xy_solve(ctx, o, true, phi0, k0, phi_out, (o->flags & NOP_OUT_DEVICE) != 0, k_out,
+                         st);
 }
 
 }  // extern "C"

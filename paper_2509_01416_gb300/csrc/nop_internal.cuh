@@ -153,6 +153,10 @@ int deeponet_project(nop_ctx* ctx, const double* field_host, float* out_host);
 int deeponet_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* status_d,
                     int* iters_d, bool predict_only, const double* src_d);
 
+// 2D x-y solver (sn2d.cu)
+int xy_solve(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* phi0, double k0,
+             double* phi_out, bool out_dev, double* k_out, nop_stats* st);
+
 // Lane split of the 1D sweep (log2 lanes per angle group, angles per lane).
 void sn1d_pick_config(int cells, int order, int* lg_ng, int* A);
 }  // namespace nop

@@ -130,6 +130,9 @@ class XYMG:
     bc: dict = field(default_factory=dict)   # faces x0, xL, y0, yL -> 0/1
 
 
+KINF_8G = 1.3
+
+
 def base_table_8g():
     """An 8-group base table: downscatter to the next two groups, upscatter
     from group 8 into 7 and within the last two groups, fission in groups 1 and
@@ -146,7 +149,10 @@ def base_table_8g():
     S[7, 6] = 0.10 * sigt[7]          # upscatter 8 -> 7
     nsf = np.array([0.020, 0.0, 0.0, 0.0, 0.010, 0.030, 0.110, 0.160])
     chi = np.array([0.70, 0.25, 0.05, 0, 0, 0, 0, 0])
-    return sigt, S, nsf, chi
+    # scale production so that the infinite-medium multiplication of the base
+    # table is KINF_8G (leakage from the 10 cm domain then brings k near 1)
+    kinf = max(np.linalg.eigvals(np.linalg.solve(np.diag(sigt) - S.T, np.outer(chi, nsf))).real)
+    return sigt, S, nsf * (KINF_8G / kinf), chi
 
 
 def config4(seed=4, n=256, L=10.0):
