@@ -742,4 +742,32 @@ int deeponet_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* sta
     return NOP_OK;
 }
 
+
+// Steps of the recast iteration shared with the FNO (operator grid of M points).
+int recast_split(nop_ctx* ctx, int B, int M, double h, const float* PS, const float* PD,
+                 const float* u, float* U, float* sig, int* flags) {
+    split_kernel<<<B, 128, 0, ctx->stream>>>(M, h, PS, PD, u, U, sig, flags);
+    NOP_CUDA_TRY(ctx, cudaGetLastError());
+    ctx->count_launch(false);
+    return NOP_OK;
+}
+
+int recast_combine(nop_ctx* ctx, int B, int M, const float* out, const float* sig,
+                   const int* flags, float* res) {
+    beta_kernel<<<(int)(((long long)B * M + 255) / 256), 256, 0, ctx->stream>>>(B, M, out, sig,
+                                                                              flags, res);
+    NOP_CUDA_TRY(ctx, cudaGetLastError());
+    ctx->count_launch(false);
+    return NOP_OK;
+}
+
+int recast_update(nop_ctx* ctx, int B, int M, double tol, const float* unew, float* u,
+                  int* status, int* iters, double* prev, int* run, int* active) {
+    recast_update_kernel<<<B, 128, 0, ctx->stream>>>(M, 0, tol, 5, unew, u, nullptr, nullptr,
+                                                    status, iters, prev, run, active);
+    NOP_CUDA_TRY(ctx, cudaGetLastError());
+    ctx->count_launch(false);
+    return NOP_OK;
+}
+
 }  // namespace nop

@@ -30,6 +30,11 @@ __global__ void __launch_bounds__(GEMM_THREADS) gemm_kernel(GemmArgs g) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wm = warp >> 1, wn = warp & 1;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    if (blockIdx.z > 0) {
+        g.A += blockIdx.z * g.sA;
+        g.B += blockIdx.z * g.sB;
+        g.C += blockIdx.z * g.sC;
+    }
     const int gq = lane >> 2, tq = lane & 3;
     float acc[2][4][4];
 #pragma unroll
@@ -175,7 +180,24 @@ int grid_for(long long n, int threads, int sm) {
 
 int gemm(nop_ctx* ctx, const GemmArgs& g) {
     if (g.M <= 0 || g.N <= 0 || g.K <= 0) return NOP_OK;
-    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
+    // grid.y is limited to 65535 row tiles: taller problems run in row chunks
+    const int max_rows = 65535 * BM;
+    if (g.M > max_rows) {
+        if (g.batch > 1) {
+            ctx->set_error("batched GEMM too tall");
+            return NOP_EINVAL;
+        }
+        for (int m0 = 0; m0 < g.M; m0 += max_rows) {
+            GemmArgs c = g;
+            c.M = std::min(max_rows, g.M - m0);
+            c.A = g.transA ? g.A + m0 : g.A + (long long)m0 * g.lda;
+            c.C = g.C + (long long)m0 * g.ldc;
+            if (g.Z) c.Z = g.Z + (long long)m0 * g.ldc;
+            NOP_TRY(gemm(ctx, c));
+        }
+        return NOP_OK;
+    }
+    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, g.batch > 1 ? g.batch : 1);
     const int mk = ctx->phase_begin(1);
     gemm_kernel<<<grid, GEMM_THREADS, 0, ctx->stream>>>(g);
     NOP_CUDA_TRY(ctx, cudaGetLastError());

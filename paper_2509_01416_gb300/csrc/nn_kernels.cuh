@@ -13,6 +13,8 @@ namespace nop {
 //   op(B) is K x N: transB = 0 -> B[k * ldb + n], 1 -> B[n * ldb + k]
 // Operands are FP32 in memory and rounded to BF16 (nearest even) when staged;
 // products accumulate in FP32.  Z (optional) receives the pre-activation.
+// batch > 1 runs that many problems with operand offsets sA, sB, sC (Z and
+// bias are not batched).
 struct GemmArgs {
     int M, N, K;
     const float* A;
@@ -26,6 +28,9 @@ struct GemmArgs {
     float* Z;
     float alpha;
     int accumulate;
+    // strided batch (blockIdx.z): element offsets between consecutive problems
+    int batch;
+    long long sA, sB, sC;
 };
 
 int gemm(nop_ctx* ctx, const GemmArgs& g);

@@ -6,13 +6,6 @@
 
 #include "nn_kernels.cuh"
 
-namespace nop {
-int fno_forward_raw(nop_ctx* ctx, int n, const float* in, int n1, int n2, float* out, bool keep);
-int fno_backward(nop_ctx* ctx, int n, int n1, int n2, const float* dout);
-int fno_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* status_d, int* iters_d,
-               bool predict_only, const double* src_d);
-}  // namespace nop
-
 using namespace nop;
 
 namespace {

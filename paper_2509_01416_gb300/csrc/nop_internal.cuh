@@ -152,6 +152,20 @@ int deeponet_backward(nop_ctx* ctx, int n, int P, const float* dout, const float
 int deeponet_project(nop_ctx* ctx, const double* field_host, float* out_host);
 int deeponet_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* status_d,
                     int* iters_d, bool predict_only, const double* src_d);
+int fno_forward_raw(nop_ctx* ctx, int n, const float* in, int n1, int n2, float* out, bool keep);
+int fno_backward(nop_ctx* ctx, int n, int n1, int n2, const float* dout);
+int fno_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* status_d, int* iters_d,
+               bool predict_only, const double* src_d);
+// Recast steps on an operator grid of M points, B instances (deeponet.cu):
+// split the source S + D u into unit-integral parts U [2B][M] (cell size h),
+// combine the operator outputs as sigma+ N[+] - sigma- N[-], and the
+// convergence bookkeeping (status 0 running, 1 converged, 3 diverged).
+int recast_split(nop_ctx* ctx, int B, int M, double h, const float* PS, const float* PD,
+                 const float* u, float* U, float* sig, int* flags);
+int recast_combine(nop_ctx* ctx, int B, int M, const float* out, const float* sig,
+                   const int* flags, float* res);
+int recast_update(nop_ctx* ctx, int B, int M, double tol, const float* unew, float* u,
+                  int* status, int* iters, double* prev, int* run, int* active);
 
 // 2D x-y solver (sn2d.cu)
 int xy_solve(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* phi0, double k0,

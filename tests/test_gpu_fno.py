@@ -1,0 +1,219 @@
+"""GPU parity of the FNO kernels (C ABI) against the FP64 oracle.
+
+The truncated transforms run as BF16 tensor-core GEMMs with FP32
+accumulation, the complex mode mixing in FP32 on BF16-rounded operands.  The
+oracle with BF16 rounding at its operand points is the tight bar (it does not
+round the DFT matrices, which the GEMMs do); plain FP64 the looser one.
+Grids are chosen non-square and modes below the Nyquist limit so that a
+transposed axis or a wrong mode index fails.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import neural as NN
+from oracle import recast as R
+from tests.helpers import oracle_slab, rel_l2, slab_batch_arrays, split
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def solver():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2509_01416_gb300 import Solver
+    s = Solver(0)
+    yield s
+    s.close()
+
+
+def _cfg1(width, modes, depth=4, proj=32, length=10.0):
+    from paper_2509_01416_gb300 import NOP_NO_FNO1D, no_config
+    return no_config(NOP_NO_FNO1D, width=width, modes=modes, depth=depth, proj=proj,
+                     length=length)
+
+
+def _cfg2(width, modes, depth=4, proj=32, length=10.0):
+    from paper_2509_01416_gb300 import NOP_NO_FNO2D, no_config
+    return no_config(NOP_NO_FNO2D, width=width, modes=modes, depth=depth, proj=proj,
+                     length=length)
+
+
+def _fno1(solver, seed, width=16, modes=8, proj=32, scale_out=1.0):
+    P = W.fno1d_init(seed, width=width, modes=modes, proj=proj)
+    P["proj2.W"] = P["proj2.W"] * scale_out
+    P["proj2.b"] = P["proj2.b"] * scale_out
+    cfg = _cfg1(width, modes, proj=proj)
+    solver.no_set(cfg, P)
+    return cfg, P
+
+
+def _fno2(solver, seed, width=8, modes=4, proj=16, scale_out=1.0):
+    P = W.fno2d_init(seed, width=width, modes=modes, proj=proj)
+    P["proj2.W"] = P["proj2.W"] * scale_out
+    P["proj2.b"] = P["proj2.b"] * scale_out
+    cfg = _cfg2(width, modes, proj=proj)
+    solver.no_set(cfg, P)
+    return cfg, P
+
+
+def _xy(solver, nx, ny, seed=0, src=True):
+    rng = np.random.default_rng(seed)
+    st = rng.uniform(0.8, 1.2, (ny, nx))
+    ss = st * rng.uniform(0.3, 0.6, (ny, nx))
+    q = rng.uniform(0.0, 1.0, (ny, nx)) if src else None
+    solver.set_xy(nx, ny, 10.0, 10.0, st.ravel(), ss.ravel(),
+                  source=None if q is None else q.ravel())
+    return st, ss, q
+
+
+def _check_grads(g, gq, gf):
+    """Gradients of a random deep ReLU net sum many products of both signs, so
+    operand rounding moves them by more than it moves the output.  The oracle
+    measures that sensitivity itself (BF16-rounded vs FP64 gradients, sens);
+    the kernels round the same operands plus the DFT matrices and the GEMM
+    inputs of the transforms, a second rounding pattern of the same size, so
+    each tensor must lie within 3 sens (at least 5e-2) of the BF16 model.  A
+    transposed operand or a sign error gives O(1)."""
+    for k in gq:
+        sens = rel_l2(gq[k], gf[k])
+        assert rel_l2(g[k], gq[k]) < max(5e-2, 3 * sens), (k, sens)
+
+
+def test_fno1d_forward_matches_oracle(solver):
+    n = 96
+    cfg, P = _fno1(solver, 1)
+    rng = np.random.default_rng(2)
+    S = rng.standard_normal((5, n))
+    got = solver.no_forward(S, coords=np.zeros(n))
+    xc = (np.arange(n) + 0.5) / n
+    q, _ = NN.fno1d_forward(P, S, xc, quant=NN.bf16_round)
+    f, _ = NN.fno1d_forward(P, S, xc)
+    assert rel_l2(got, q) < 1e-2
+    assert rel_l2(got, f) < 3e-2
+
+
+def test_fno1d_gradients_match_oracle(solver):
+    n = 64
+    cfg, P = _fno1(solver, 3, width=16, modes=12)
+    rng = np.random.default_rng(4)
+    S = rng.standard_normal((4, n))
+    Y = rng.standard_normal((4, n))
+    loss, g = solver.no_loss_grad(S, Y, coords=np.zeros(n))
+    xc = (np.arange(n) + 0.5) / n
+    out, cache = NN.fno1d_forward(P, S, xc, quant=NN.bf16_round)
+    l0, dout = NN.mse(out, Y)
+    g0 = NN.fno1d_backward(P, cache, dout, quant=NN.bf16_round)
+    of, cf = NN.fno1d_forward(P, S, xc)
+    gf = NN.fno1d_backward(P, cf, NN.mse(of, Y)[1])
+    assert abs(loss - l0) < 1e-2 * l0
+    _check_grads(g, g0, gf)
+
+
+def test_fno2d_forward_matches_oracle(solver):
+    nx, ny = 24, 16
+    _xy(solver, nx, ny)
+    cfg, P = _fno2(solver, 5)
+    rng = np.random.default_rng(6)
+    S = rng.standard_normal((3, ny, nx))
+    got = solver.no_forward(S.reshape(3, -1)).reshape(3, ny, nx)
+    yc, xc = (np.arange(ny) + 0.5) / ny, (np.arange(nx) + 0.5) / nx
+    q, _ = NN.fno2d_forward(P, S, yc, xc, quant=NN.bf16_round)
+    f, _ = NN.fno2d_forward(P, S, yc, xc)
+    assert rel_l2(got, q) < 1e-2
+    assert rel_l2(got, f) < 3e-2
+
+
+def test_fno2d_gradients_match_oracle(solver):
+    nx, ny = 20, 12
+    _xy(solver, nx, ny)
+    cfg, P = _fno2(solver, 7, width=8, modes=3)
+    rng = np.random.default_rng(8)
+    S = rng.standard_normal((2, ny, nx))
+    Y = rng.standard_normal((2, ny, nx))
+    loss, g = solver.no_loss_grad(S.reshape(2, -1), Y.reshape(2, -1))
+    yc, xc = (np.arange(ny) + 0.5) / ny, (np.arange(nx) + 0.5) / nx
+    out, cache = NN.fno2d_forward(P, S, yc, xc, quant=NN.bf16_round)
+    l0, dout = NN.mse(out, Y)
+    g0 = NN.fno2d_backward(P, cache, dout, quant=NN.bf16_round)
+    of, cf = NN.fno2d_forward(P, S, yc, xc)
+    gf = NN.fno2d_backward(P, cf, NN.mse(of, Y)[1])
+    assert abs(loss - l0) < 1e-2 * l0
+    _check_grads(g, g0, gf)
+
+
+def test_fno1d_training_lowers_the_loss(solver):
+    n = 64
+    cfg, P = _fno1(solver, 9, width=16, modes=8)
+    rng = np.random.default_rng(10)
+    S = rng.standard_normal((40, n))
+    Y = np.cumsum(S, axis=1) / n          # a smooth linear target map
+    hist = solver.no_train(S, Y, coords=np.zeros(n), steps=200, batch=10, lr=2e-3)
+    assert np.all(np.isfinite(hist))
+    assert hist[-20:].mean() < 0.5 * hist[:20].mean()
+
+
+def _equal_slabs(solver, I, count, seed):
+    insts = [W.slab_instance(np.random.default_rng(seed + b), I, 8) for b in range(count)]
+    n, wdt, order, sigt, sigs, src, _ = slab_batch_arrays(insts)
+    solver.set_slabs(n, wdt, order, sigt, sigs, source=src)
+    return insts
+
+
+def test_fno1d_predict_and_recast_match_oracle(solver):
+    insts = _equal_slabs(solver, 80, 3, seed=40)
+    cfg, P = _fno1(solver, 11, width=16, modes=8, scale_out=2e-3)
+    op = R.FNOOp1D(P, 10.0, quant=NN.bf16_round)
+    rng = np.random.default_rng(12)
+    srcs = [rng.uniform(-0.5, 1.0, s.I) for s in insts]
+    got = split(solver.no_predict(np.concatenate(srcs)), insts)
+    for src, g in zip(srcs, got):
+        assert rel_l2(g, op(src[None])[0]) < 1e-2
+    phi, info = solver.recast_iterate(tol=1e-5, itmax=100)
+    for b, (s, g) in enumerate(zip(insts, split(phi, insts))):
+        pr = oracle_slab(s)
+        delta = (pr.sigs[0, 0] - W.P_STAR[1]) - (pr.sigt[0] - W.P_STAR[0])
+        ref, it, st = R.recast_grid(op, pr.Q[0], delta, tol=1e-5, itmax=100)
+        assert st == R.OK and info["status"][b] == 0
+        assert abs(int(info["iterations"][b]) - it) <= 1
+        assert rel_l2(g, ref) < 1e-2
+
+
+def test_fno1d_recast_rejects_unequal_grids(solver):
+    insts = [W.slab_instance(np.random.default_rng(b), I, 8) for b, I in enumerate([64, 80])]
+    n, wdt, order, sigt, sigs, src, _ = slab_batch_arrays(insts)
+    solver.set_slabs(n, wdt, order, sigt, sigs, source=src)
+    _fno1(solver, 13, scale_out=2e-3)
+    from paper_2509_01416_gb300 import NopError
+    with pytest.raises(NopError):
+        solver.recast_iterate(tol=1e-5, itmax=10)
+
+
+def test_fno2d_recast_matches_oracle(solver):
+    nx, ny = 24, 16
+    st, ss, q = _xy(solver, nx, ny, seed=3)
+    cfg, P = _fno2(solver, 14, scale_out=2e-3)
+    op = R.FNOOp2D(P, 10.0, 10.0, quant=NN.bf16_round)
+    phi, info = solver.recast_iterate(tol=1e-5, itmax=100)
+    delta = (ss - W.P_STAR[1]) - (st - W.P_STAR[0])
+    ref, it, status = R.recast_grid(op, q, delta, tol=1e-5, itmax=100)
+    assert status == R.OK and info["status"][0] == 0
+    assert abs(int(info["iterations"][0]) - it) <= 1
+    assert rel_l2(phi.reshape(ny, nx), ref) < 1e-2
+
+
+def test_fno_warm_start_keeps_the_answer(solver):
+    insts = _equal_slabs(solver, 128, 4, seed=50)
+    _fno1(solver, 15, scale_out=2e-3)
+    plain, _ = solver.solve_fixed_source(tol=1e-6, precision=0)
+    warm, wi = solver.solve_fixed_source(tol=1e-6, precision=0, warm_start=1)
+    assert wi["recast_status"] in (0, -4)
+    assert rel_l2(warm, plain) < 2e-5
+    nx, ny = 24, 16
+    _xy(solver, nx, ny, seed=4)
+    _fno2(solver, 16, scale_out=2e-3)
+    plain, _ = solver.solve_fixed_source(tol=1e-7, precision=1)
+    warm, wi = solver.solve_fixed_source(tol=1e-7, precision=1, warm_start=1)
+    assert rel_l2(warm, plain) < 1e-5
