@@ -302,6 +302,25 @@ int nop_no_predict(nop_ctx *ctx, const double *src, double *phi_out);
 int nop_recast_iterate(nop_ctx *ctx, double tol, int itmax, int flags, double *phi_out,
                        nop_stats *stats);
 
+/* Simple-preconditioning warm start of an eigenproblem (App. A2 Eq. A5): a
+ * power iteration whose inner solve is one application of the trained
+ * operator per group and outer step, group g taking the recast source
+ *   chi_g F / k + sum_{g' != g} Sigma_s^{g'->g} phi_g' + delta_g phi_g,
+ *   delta_g = (Sigma_s^{g->g} - Sigma_s*) - (Sigma_t,g - Sigma_t*),
+ * (newest fluxes of the groups already visited), then k <- k P, phi <- phi / P
+ * with P the production integral.  Starts from the flat flux at unit
+ * production and k = 1; an instance stops when |dk|/k <= tol and the relative
+ * L2 change of its flux <= tol, or after itmax outer steps.  The operator is
+ * the one installed (FNO-1D needs instances of equal cell counts).
+ * phi_out: host [G*C] doubles (device with NOP_OUT_DEVICE in flags), unit
+ * production per instance; k_out: host [n_inst].  Instances whose iteration
+ * went non-finite get the plain guess (flat flux, k = 1) and NOP_EDIVERGE.
+ * stats: recast_iterations (max outer steps), recast_status, inst_status,
+ * inst_iterations.  Nothing of the problem is modified.  The result seeds
+ * nop_solve_eigen with warm_start = NOP_WARM_RECAST (Eq. A6). */
+int nop_sp_eigen(nop_ctx *ctx, double tol, int itmax, int flags, double *phi_out,
+                 double *k_out, nop_stats *stats);
+
 /* --------------------------------------------------- allocation-free solve */
 
 #define NOP_NOALLOC_MAX_CELLS  65536

@@ -288,4 +288,15 @@ class Solver:
             self._check(rc, "nop_solve_eigen")
         return k, phi, {"rc": rc, "inner": it, "status": ss, "outer": st.max_outer,
                         "max_change": st.max_change,
-                        "recast_iterations": st.recast_iterations}
+                        "recast_iterations": st.recast_iterations,
+                        "recast_status": st.recast_status}
+
+    def sp_eigen(self, tol=1e-4, itmax=200):
+        """Simple-preconditioning eigen warm start alone: (k per instance, phi, info)."""
+        phi = np.zeros(self.G * self.C)
+        k = np.zeros(self.n_inst)
+        st, it, ss = self._stats()
+        self._check(self._L.nop_sp_eigen(self.h, tol, itmax, 0, phi.ctypes.data, k.ctypes.data,
+                                         C.byref(st)), "nop_sp_eigen")
+        return k, phi, {"iterations": it, "status": ss, "max_iterations": st.recast_iterations,
+                        "recast_status": st.recast_status}

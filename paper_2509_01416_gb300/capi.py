@@ -102,6 +102,8 @@ SIGNATURES = {
     "nop_no_predict": (C.c_int, [C.c_void_p, _dp, _dp]),
     "nop_recast_iterate": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_void_p,
                                      C.POINTER(nop_stats)]),
+    "nop_sp_eigen": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_void_p,
+                               C.c_void_p, C.POINTER(nop_stats)]),
     "nop_get_timing": (C.c_int, [C.c_void_p, C.POINTER(nop_timings)]),
     "nop_solve_eigen": (C.c_int, [C.c_void_p, C.POINTER(nop_solve_opts), C.c_void_p,
                                   C.c_double, C.c_void_p, C.c_void_p,

@@ -41,6 +41,8 @@ int nop_ctx::scratch(const char* name, size_t bytes, void** out) {
 
 int nop_ctx::phase_begin(int phase) {
     if (!timing) return -1;
+    // phases do not nest: an inner phase belongs to the enclosing one
+    if (phase_depth++ > 0) return -2;
     Mark m;
     m.phase = phase;
     for (cudaEvent_t* e : {&m.a, &m.b}) {
@@ -48,6 +50,7 @@ int nop_ctx::phase_begin(int phase) {
             *e = event_pool.back();
             event_pool.pop_back();
         } else if (cudaEventCreate(e) != cudaSuccess) {
+            --phase_depth;
             return -1;
         }
     }
@@ -57,6 +60,8 @@ int nop_ctx::phase_begin(int phase) {
 }
 
 void nop_ctx::phase_end(int mark) {
+    if (mark == -1) return;
+    if (phase_depth > 0) --phase_depth;
     if (mark < 0 || mark >= (int)marks.size()) return;
     cudaEventRecord(marks[mark].b, stream);
 }
@@ -150,6 +155,7 @@ int nop_set_timing(nop_ctx* ctx, int enable) {
         ctx->event_pool.push_back(m.b);
     }
     ctx->marks.clear();
+    ctx->phase_depth = 0;
     ctx->launches = ctx->sweep_launches = 0;
     ctx->cell_angle_updates = 0;
     ctx->timing = enable != 0;
@@ -360,6 +366,7 @@ static int check_opts(nop_ctx* ctx, const nop_solve_opts* o, bool eigen) {
 int nop_solve_fixed_source(nop_ctx* ctx, const nop_solve_opts* o, const double* phi0,
                            double* phi_out, nop_stats* st) {
     if (!ctx) return NOP_EINVAL;
+    ctx->phase_depth = 0;
     NOP_TRY(check_opts(ctx, o, false));
     if (!ctx->has_problem || !ctx->has_source) {
         ctx->set_error("fixed-source solve needs a problem with a source");
@@ -405,6 +412,7 @@ int nop_solve_fixed_source(nop_ctx* ctx, const nop_solve_opts* o, const double* 
 int nop_solve_eigen(nop_ctx* ctx, const nop_solve_opts* o, const double* phi0, double k0,
                     double* phi_out, double* k_out, nop_stats* st) {
     if (!ctx) return NOP_EINVAL;
+    ctx->phase_depth = 0;
     NOP_TRY(check_opts(ctx, o, true));
     if (!ctx->has_problem || !ctx->has_fission) {
         ctx->set_error("eigen solve needs a problem with nu_sigma_f and chi");
@@ -415,18 +423,45 @@ int nop_solve_eigen(nop_ctx* ctx, const nop_solve_opts* o, const double* phi0, d
         st->recast_iterations = 0;
         st->recast_status = NOP_OK;
     }
-    if (o->warm_start != NOP_WARM_NONE) {
-        ctx->set_error("warm start requested but no neural operator is loaded");
-        return NOP_ESTATE;
+    const int B = ctx->geometry == NOP_GEOM_SLAB ? ctx->slab.n_inst : 1;
+    std::vector<double> k0v(B, k0 > 0 ? k0 : 1.0);
+    bool phi0_dev = (o->flags & NOP_PHI0_DEVICE) != 0;
+    if (o->warm_start == NOP_WARM_RECAST) {
+        // App. A2: the simple-preconditioning result (Eq. A5) seeds the
+        // model-based power iteration (Eq. A6)
+        if (!ctx->no.loaded) {
+            ctx->set_error("warm start requested but no neural operator is loaded");
+            return NOP_ESTATE;
+        }
+        void* p;
+        NOP_TRY(ctx->scratch("ws_phi0", sizeof(double) * ctx->G * ctx->C, &p));
+        std::vector<int> sst, sit;
+        NOP_TRY(nop::sp_eigen(ctx, o->recast_tol > 0 ? o->recast_tol : 1e-4,
+                              o->recast_itmax > 0 ? o->recast_itmax : 200, (double*)p, &k0v, &sst,
+                              &sit));
+        phi0 = (const double*)p;
+        phi0_dev = true;
+        if (st) {
+            int worst = NOP_OK, imax = 0;
+            for (int b = 0; b < B; ++b) {
+                const int code = sst[b] == 3 ? NOP_EDIVERGE : (sst[b] == 1 ? NOP_OK : NOP_ENOCONV);
+                if (code == NOP_EDIVERGE || (code != NOP_OK && worst == NOP_OK)) worst = code;
+                imax = std::max(imax, sit[b]);
+            }
+            st->recast_iterations = imax;
+            st->recast_status = worst;
+        }
+    } else if (o->warm_start != NOP_WARM_NONE) {
+        ctx->set_error("unknown warm start");
+        return NOP_EINVAL;
     }
-    if (ctx->geometry == NOP_GEOM_SLAB) {
-        std::vector<double> k0v(ctx->slab.n_inst, k0 > 0 ? k0 : 1.0);
-        return nop::sn1d_solve(ctx, o, true, phi0, (o->flags & NOP_PHI0_DEVICE) != 0,
-                               k0v.data(), phi_out, (o->flags & NOP_OUT_DEVICE) != 0, k_out,
-                               st);
-    }
-    return nop::xy_solve(ctx, o, true, phi0, k0, phi_out, (o->flags & NOP_OUT_DEVICE) != 0, k_out,
-                         st);
+    if (ctx->geometry == NOP_GEOM_SLAB)
+        return nop::sn1d_solve(ctx, o, true, phi0, phi0_dev, k0v.data(), phi_out,
+                               (o->flags & NOP_OUT_DEVICE) != 0, k_out, st);
+    nop_solve_opts o2 = *o;
+    if (phi0_dev) o2.flags |= NOP_PHI0_DEVICE;
+    return nop::xy_solve(ctx, &o2, true, phi0, k0v[0], phi_out, (o->flags & NOP_OUT_DEVICE) != 0,
+                         k_out, st);
 }
 
 }  // extern "C"

@@ -339,4 +339,43 @@ int nop_recast_iterate(nop_ctx* ctx, double tol, int itmax, int flags, double* p
     return NOP_OK;
 }
 
+int nop_sp_eigen(nop_ctx* ctx, double tol, int itmax, int flags, double* phi_out, double* k_out,
+                 nop_stats* st) {
+    if (!ctx || !phi_out || !k_out || !(tol > 0) || itmax < 1) return NOP_EINVAL;
+    if (!ctx->no.loaded || !ctx->has_problem || !ctx->has_fission) return NOP_ESTATE;
+    NOP_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    ctx->phase_depth = 0;
+    const long long GC = (long long)ctx->G * ctx->C;
+    double* pd = phi_out;
+    void* p;
+    if (!(flags & NOP_OUT_DEVICE)) {
+        NOP_TRY(ctx->scratch("sp_phi", sizeof(double) * GC, &p));
+        pd = (double*)p;
+    }
+    std::vector<double> k;
+    std::vector<int> status, iters;
+    NOP_TRY(sp_eigen(ctx, tol, itmax, pd, &k, &status, &iters));
+    if (!(flags & NOP_OUT_DEVICE)) {
+        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(phi_out, pd, sizeof(double) * GC, cudaMemcpyDeviceToHost,
+                                          ctx->stream));
+        NOP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    const int B = (int)k.size();
+    int worst = NOP_OK, imax = 0;
+    for (int b = 0; b < B; ++b) {
+        k_out[b] = k[b];
+        const int code = status[b] == 3 ? NOP_EDIVERGE : (status[b] == 1 ? NOP_OK : NOP_ENOCONV);
+        if (code == NOP_EDIVERGE || (code != NOP_OK && worst == NOP_OK)) worst = code;
+        imax = std::max(imax, iters[b]);
+        if (st && st->inst_status) st->inst_status[b] = code;
+        if (st && st->inst_iterations) st->inst_iterations[b] = iters[b];
+    }
+    if (st) {
+        st->recast_iterations = imax;
+        st->recast_status = worst;
+        st->status = worst;
+    }
+    return NOP_OK;
+}
+
 }  // extern "C"

@@ -108,6 +108,7 @@ struct nop_ctx {
         cudaEvent_t a, b;
     };
     std::vector<Mark> marks;
+    int phase_depth = 0;
     std::vector<cudaEvent_t> event_pool;
     long long launches = 0, sweep_launches = 0;
     double cell_angle_updates = 0;
@@ -166,6 +167,12 @@ int recast_combine(nop_ctx* ctx, int B, int M, const float* out, const float* si
                    const int* flags, float* res);
 int recast_update(nop_ctx* ctx, int B, int M, double tol, const float* unew, float* u,
                   int* status, int* iters, double* prev, int* run, int* active);
+
+// Simple-preconditioning eigen warm start (sp_eigen.cu): phi_d [G*C] device
+// out (unit production), k/status/iterations per instance on the host.
+// status: 0 cap reached, 1 converged, 3 diverged (phi flat, k = 1).
+int sp_eigen(nop_ctx* ctx, double tol, int itmax, double* phi_d, std::vector<double>* k_h,
+             std::vector<int>* status_h, std::vector<int>* iters_h);
 
 // 2D x-y solver (sn2d.cu)
 int xy_solve(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* phi0, double k0,

@@ -26,6 +26,45 @@ def deeponet_training_set(solver, cfg, sources, order=32, tol=1e-7, itmax=100000
     return U, X, phi.reshape(n, I), info
 
 
+def fno1d_training_set(solver, cfg, sources, order=32, tol=1e-7, itmax=100000):
+    """Solve the p* slab for every source row (n x I cells over cfg.length).
+
+    Returns (inputs [n, I] = the sources, targets [n, I] = the fluxes, info):
+    the FNO-1D maps a source on the grid to the flux on the same grid.
+    """
+    n, I = sources.shape
+    st, ss = cfg.sigma_t_star, cfg.sigma_s_star
+    solver.set_slabs(np.full(n, I), np.full(n, cfg.length), np.full(n, order),
+                     np.full(n * I, st), np.full(n * I, ss), source=sources.reshape(-1))
+    phi, info = solver.solve_fixed_source(tol=tol, itmax=itmax, precision=0)
+    return sources.astype(np.float32), phi.reshape(n, I), info
+
+
+def fno2d_training_set(solver, cfg, sources, tol=1e-7, itmax=100000, bc=(0, 0, 0, 0)):
+    """Solve the p* square (cfg.length, vacuum unless bc says otherwise) for
+    every source field (n x ny x nx, row-major [y][x]); returns (inputs [n, ny*nx],
+    targets [n, ny*nx])."""
+    n, ny, nx = sources.shape
+    st, ss = cfg.sigma_t_star, cfg.sigma_s_star
+    Y = np.zeros((n, ny * nx))
+    for b in range(n):
+        solver.set_xy(nx, ny, cfg.length, cfg.length, np.full(nx * ny, st),
+                      np.full(nx * ny, ss), source=sources[b].reshape(-1), bc=bc)
+        phi, _ = solver.solve_fixed_source(tol=tol, itmax=itmax, precision=0)
+        Y[b] = phi
+    return sources.reshape(n, -1).astype(np.float32), Y
+
+
+def train_fno(solver, S, Y, steps, batch, seed, lr=1e-3):
+    """Adam on FNO pairs (S, Y) with a seeded sample order (grid from S's width
+    for FNO-1D, from the current x-y problem for FNO-2D)."""
+    rng = np.random.default_rng(seed)
+    n = S.shape[0]
+    order = np.concatenate([rng.permutation(n) for _ in range((steps * batch) // n + 1)])
+    return solver.no_train(S, Y, np.zeros(S.shape[1], dtype=np.float32), steps=steps,
+                           batch=batch, lr=lr, order=order[:steps * batch])
+
+
 def train(solver, U, X, Y, steps, batch, seed, lr=1e-3):
     """Adam on (U, X, Y) with a seeded sample order; returns the loss history."""
     rng = np.random.default_rng(seed)
