@@ -140,13 +140,19 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--train-steps", type=int, default=3000)
+    ap.add_argument("--train-steps", type=int, default=3000,
+                    help="Adam steps of the operator's training (0: untrained operator, "
+                         "no training set; for profiling runs)")
+    ap.add_argument("--instances", type=int, default=0,
+                    help="solve only the first N instances of the batch (profiling aid)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     insts = W.config5(seed=5 + rank)
+    if args.instances > 0:
+        insts = insts[:args.instances]
     cores = os.cpu_count() or 1
 
     if args.impl == "reference":
@@ -183,8 +189,11 @@ def main():
     torch.cuda.synchronize()
     t_tr = time.perf_counter()
     s.no_set(cfg, W.deeponet_init(1000 + rank))
-    U, Xc, Y, _ = TR.deeponet_training_set(s, cfg, W.training_sources(2000 + rank, 2000, 512))
-    hist = TR.train(s, U, Xc, Y, steps=args.train_steps, batch=100, seed=3000 + rank)
+    hist = None
+    if args.train_steps > 0:
+        U, Xc, Y, _ = TR.deeponet_training_set(s, cfg,
+                                               W.training_sources(2000 + rank, 2000, 512))
+        hist = TR.train(s, U, Xc, Y, steps=args.train_steps, batch=100, seed=3000 + rank)
     train_s = time.perf_counter() - t_tr
 
     s.set_slabs(n, wdt, order, sigt, sigs, source=src)
@@ -208,12 +217,16 @@ def main():
         torch.cuda.synchronize()
         if clk:
             clk.__enter__()
+            # the timed warm-start region is the one a profiler started with
+            # --profile-from-start off records
+            torch.cuda.profiler.start()
         ev0.record(stream)
         for _ in range(steps):
             info = step(warm)
         ev1.record(stream)
         torch.cuda.synchronize()
         if clk:
+            torch.cuda.profiler.stop()
             clk.__exit__()
         barrier()
         tm = s.timing()
@@ -285,7 +298,9 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "precision": {"sweep": "f32", "norms": "f64"},
         "data": "synthetic (seeded; paper's samples unpublished)",
-        "config": {"workload": WORKLOAD, "instances_per_gpu": B, "cells_per_gpu": Ctot,
+        "config": {"workload": WORKLOAD if B == 4096 else
+                               "first %d of: %s" % (B, WORKLOAD),
+                   "instances_per_gpu": B, "cells_per_gpu": Ctot,
                    "l2": "inputs larger than L2: %.0f MB resident per GPU" %
                          ((Ctot * (3 * 8 + 24)) / 1e6),
                    "warm_start": "DeepONet (128 sensors, 4x128, p=128, BF16) recast, "
@@ -300,7 +315,8 @@ def main():
                        "operator_ms_per_step": tm["operator_ms"] / args.steps,
                        "sweep_ms_per_step": tm["sweep_ms"] / args.steps,
                        "speedup_vs_plain": value / plain_value if plain_value else None},
-        "training": {"samples": 2000, "steps": args.train_steps, "batch": 100,
+        "training": None if hist is None else
+                    {"samples": 2000, "steps": args.train_steps, "batch": 100,
                      "seconds": train_s, "loss_first": float(hist[0]),
                      "loss_last": float(np.mean(hist[-20:]))},
         "clocks": ck,

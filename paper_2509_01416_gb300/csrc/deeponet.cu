@@ -217,12 +217,14 @@ __global__ void split_kernel(int M, double h, const float* PS, const float* PD, 
                              float* U, float* sig, int* flags) {
     __shared__ double red[2][32];
     const int b = blockIdx.x;
-    double ap = 0.0, an = 0.0;
+    // FP32 partial sums per thread, FP64 across threads
+    float apf = 0.f, anf = 0.f;
     for (int m = threadIdx.x; m < M; m += blockDim.x) {
         const float s = PS[(long long)b * M + m] + PD[(long long)b * M + m] * u[(long long)b * M + m];
-        if (s > 0.f) ap += s;
-        else an -= s;
+        if (s > 0.f) apf += s;
+        else anf -= s;
     }
+    double ap = apf, an = anf;
     for (int o = 16; o > 0; o >>= 1) {
         ap += __shfl_xor_sync(0xffffffffu, ap, o);
         an += __shfl_xor_sync(0xffffffffu, an, o);
@@ -239,10 +241,11 @@ __global__ void split_kernel(int M, double h, const float* PS, const float* PD, 
     }
     sp *= h;
     sn *= h;
+    const float ip = sp > 0 ? (float)(1.0 / sp) : 0.f, in = sn > 0 ? (float)(1.0 / sn) : 0.f;
     for (int m = threadIdx.x; m < M; m += blockDim.x) {
         const float s = PS[(long long)b * M + m] + PD[(long long)b * M + m] * u[(long long)b * M + m];
-        U[(2LL * b) * M + m] = sp > 0 ? (float)(fmax((double)s, 0.0) / sp) : 0.f;
-        U[(2LL * b + 1) * M + m] = sn > 0 ? (float)(fmax(-(double)s, 0.0) / sn) : 0.f;
+        U[(2LL * b) * M + m] = fmaxf(s, 0.f) * ip;
+        U[(2LL * b + 1) * M + m] = fmaxf(-s, 0.f) * in;
     }
     if (threadIdx.x == 0) {
         sig[2 * b] = (float)sp;
@@ -272,12 +275,13 @@ __global__ void recast_update_kernel(int M, int p, double tol, int diverge_run, 
     __shared__ double red[2][32];
     const int b = blockIdx.x;
     if (status[b] != 0) return;
-    double d2 = 0.0, n2 = 0.0;
+    float d2f = 0.f, n2f = 0.f;
     for (int m = threadIdx.x; m < M; m += blockDim.x) {
-        const double a = unew[(long long)b * M + m], o = u[(long long)b * M + m];
-        d2 += (a - o) * (a - o);
-        n2 += a * a;
+        const float a = unew[(long long)b * M + m], o = u[(long long)b * M + m];
+        d2f += (a - o) * (a - o);
+        n2f += a * a;
     }
+    double d2 = d2f, n2 = n2f;
     for (int o = 16; o > 0; o >>= 1) {
         d2 += __shfl_xor_sync(0xffffffffu, d2, o);
         n2 += __shfl_xor_sync(0xffffffffu, n2, o);
@@ -353,7 +357,7 @@ __global__ void trunk_dot_kernel(long long c0, int n, int p, const float* Tn, co
 // layer 1 (elementwise, K = 1), layers 2-4 on mma.sync (BF16 operands, FP32
 // accumulation, activations rounded to BF16 between layers like the generic
 // GEMM), then the inner product with its instance's coefficients.
-constexpr int FT_W = 128, FT_PAD = 8, FT_WARPS = 8, FT_PTS = 16 * FT_WARPS;
+constexpr int FT_W = 128, FT_PAD = 8, FT_WARPS = 8, FT_MT = 2, FT_PTS = 16 * FT_MT * FT_WARPS;
 
 __device__ __forceinline__ void ft_mma(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
                                        uint32_t b1) {
@@ -364,6 +368,8 @@ __device__ __forceinline__ void ft_mma(float (&c)[4], const uint32_t (&a)[4], ui
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// Every warp owns 32 points (two m16 tiles), so each weight fragment loaded
+// from shared memory feeds two tensor-core instructions.
 __global__ void __launch_bounds__(32 * FT_WARPS) trunk_fused_kernel(
     long long C, int B, const long long* cell_off, const int* ncell, const float* W1,
     const float* b1, const float* W2, const float* b2, const float* W3, const float* b3,
@@ -383,18 +389,19 @@ __global__ void __launch_bounds__(32 * FT_WARPS) trunk_fused_kernel(
         Ws[2][n][k] = __float2bfloat16_rn(W4[e]);
     }
     for (int n = tid; n < FT_W; n += blockDim.x) {
-        w1s[n] = W1[n];
+        // the trunk input weights are rounded to BF16 like any GEMM operand
+        w1s[n] = __bfloat162float(__float2bfloat16_rn(W1[n]));
         bs[0][n] = b1[n];
         bs[1][n] = b2[n];
         bs[2][n] = b3[n];
         bs[3][n] = b4[n];
     }
     __syncthreads();
+    const int r0 = warp * 16 * FT_MT;
     for (long long t0 = (long long)blockIdx.x * FT_PTS; t0 < C; t0 += (long long)gridDim.x * FT_PTS) {
-        // owning instance and coordinate of the warp's 16 points, one lane each
-        const int r0 = warp * 16;
+        // owning instance and coordinate of the warp's 32 points, one lane each
         float xl = 0.f;
-        if (lane < 16) {
+        {
             const long long c = t0 + r0 + lane;
             int b = -1;
             if (c < C) {
@@ -409,75 +416,84 @@ __global__ void __launch_bounds__(32 * FT_WARPS) trunk_fused_kernel(
             }
             pinst[r0 + lane] = b;
         }
-        // layer 1 for the warp's 16 points: h = relu(x w1 + b1), BF16
-        for (int rr = 0; rr < 16; ++rr) {
+        // layer 1 for the warp's points: h = relu(x w1 + b1), BF16
+        for (int rr = 0; rr < 16 * FT_MT; ++rr) {
             const float x = __shfl_sync(0xffffffffu, xl, rr);
-            // the trunk input is rounded to BF16 like any GEMM operand
             const float xb = __bfloat162float(__float2bfloat16_rn(x));
-            for (int n = lane; n < FT_W; n += 32) {
-                const float w = __bfloat162float(__float2bfloat16_rn(w1s[n]));
-                H[r0 + rr][n] = __float2bfloat16_rn(fmaxf(xb * w + bs[0][n], 0.f));
-            }
+            for (int n = lane; n < FT_W; n += 32)
+                H[r0 + rr][n] = __float2bfloat16_rn(fmaxf(xb * w1s[n] + bs[0][n], 0.f));
         }
         __syncwarp();
-        float acc[16][4];
+        float acc[FT_MT][16][4];
         for (int l = 0; l < 3; ++l) {
 #pragma unroll
-            for (int nt = 0; nt < 16; ++nt)
+            for (int mt = 0; mt < FT_MT; ++mt)
 #pragma unroll
-                for (int c4 = 0; c4 < 4; ++c4) acc[nt][c4] = 0.f;
+                for (int nt = 0; nt < 16; ++nt)
 #pragma unroll
+                    for (int c4 = 0; c4 < 4; ++c4) acc[mt][nt][c4] = 0.f;
+#pragma unroll 2
             for (int kk = 0; kk < FT_W; kk += 16) {
-                uint32_t af[4];
-                af[0] = *(const uint32_t*)&H[r0 + gq][kk + 2 * tq];
-                af[1] = *(const uint32_t*)&H[r0 + gq + 8][kk + 2 * tq];
-                af[2] = *(const uint32_t*)&H[r0 + gq][kk + 2 * tq + 8];
-                af[3] = *(const uint32_t*)&H[r0 + gq + 8][kk + 2 * tq + 8];
+                uint32_t af[FT_MT][4];
+#pragma unroll
+                for (int mt = 0; mt < FT_MT; ++mt) {
+                    const int r = r0 + mt * 16 + gq;
+                    af[mt][0] = *(const uint32_t*)&H[r][kk + 2 * tq];
+                    af[mt][1] = *(const uint32_t*)&H[r + 8][kk + 2 * tq];
+                    af[mt][2] = *(const uint32_t*)&H[r][kk + 2 * tq + 8];
+                    af[mt][3] = *(const uint32_t*)&H[r + 8][kk + 2 * tq + 8];
+                }
 #pragma unroll
                 for (int nt = 0; nt < 16; ++nt) {
                     const int n = nt * 8 + gq;
                     const uint32_t b0 = *(const uint32_t*)&Ws[l][n][kk + 2 * tq];
                     const uint32_t b1v = *(const uint32_t*)&Ws[l][n][kk + 2 * tq + 8];
-                    ft_mma(acc[nt], af, b0, b1v);
+#pragma unroll
+                    for (int mt = 0; mt < FT_MT; ++mt) ft_mma(acc[mt][nt], af[mt], b0, b1v);
                 }
             }
             __syncwarp();
             if (l < 2) {
 #pragma unroll
-                for (int nt = 0; nt < 16; ++nt)
+                for (int mt = 0; mt < FT_MT; ++mt)
 #pragma unroll
-                    for (int h2 = 0; h2 < 2; ++h2)
+                    for (int nt = 0; nt < 16; ++nt)
 #pragma unroll
-                        for (int cc = 0; cc < 2; ++cc) {
-                            const int n = nt * 8 + 2 * tq + cc;
-                            H[r0 + gq + 8 * h2][n] =
-                                __float2bfloat16_rn(fmaxf(acc[nt][2 * h2 + cc] + bs[l + 1][n], 0.f));
-                        }
+                        for (int h2 = 0; h2 < 2; ++h2)
+#pragma unroll
+                            for (int cc = 0; cc < 2; ++cc) {
+                                const int n = nt * 8 + 2 * tq + cc;
+                                H[r0 + mt * 16 + gq + 8 * h2][n] = __float2bfloat16_rn(
+                                    fmaxf(acc[mt][nt][2 * h2 + cc] + bs[l + 1][n], 0.f));
+                            }
                 __syncwarp();
             }
         }
         // output layer values + bias, inner product with the instance's beta
 #pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2) {
-            const int row = r0 + gq + 8 * h2;
-            const int b = pinst[row];
-            float d = 0.f;
-            if (b >= 0 && (!status || status[b] != 3)) {
+        for (int mt = 0; mt < FT_MT; ++mt)
 #pragma unroll
-                for (int nt = 0; nt < 16; ++nt)
+            for (int h2 = 0; h2 < 2; ++h2) {
+                const int row = r0 + mt * 16 + gq + 8 * h2;
+                const int b = pinst[row];
+                float d = 0.f;
+                if (b >= 0 && (!status || status[b] != 3)) {
 #pragma unroll
-                    for (int cc = 0; cc < 2; ++cc) {
-                        const int n = nt * 8 + 2 * tq + cc;
-                        const float tv = acc[nt][2 * h2 + cc] + bs[3][n];
-                        d += __bfloat162float(__float2bfloat16_rn(tv)) *
-                             __bfloat162float(__float2bfloat16_rn(beta_keep[(long long)b * FT_W + n]));
-                    }
+                    for (int nt = 0; nt < 16; ++nt)
+#pragma unroll
+                        for (int cc = 0; cc < 2; ++cc) {
+                            const int n = nt * 8 + 2 * tq + cc;
+                            const float tv = acc[mt][nt][2 * h2 + cc] + bs[3][n];
+                            d += __bfloat162float(__float2bfloat16_rn(tv)) *
+                                 __bfloat162float(
+                                     __float2bfloat16_rn(beta_keep[(long long)b * FT_W + n]));
+                        }
+                }
+                d += __shfl_xor_sync(0xffffffffu, d, 1);
+                d += __shfl_xor_sync(0xffffffffu, d, 2);
+                const long long c = t0 + row;
+                if (tq == 0 && c < C) phi[c] = d;
             }
-            d += __shfl_xor_sync(0xffffffffu, d, 1);
-            d += __shfl_xor_sync(0xffffffffu, d, 2);
-            const long long c = t0 + row;
-            if (tq == 0 && c < C) phi[c] = d;
-        }
         __syncwarp();
     }
 }
@@ -639,12 +655,20 @@ int deeponet_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* sta
     NOP_TRY(mlp_forward(ctx, 1, M, Xb, &Tn, false));
     NOP_CUDA_TRY(ctx, cudaMemcpyAsync(Tref, Tn, sizeof(float) * (size_t)M * p,
                                       cudaMemcpyDeviceToDevice, ctx->stream));
-    int* active_h = nullptr;
-    NOP_CUDA_TRY(ctx, cudaMallocHost(&active_h, sizeof(int)));
     const int imax = predict_only ? 1 : itmax;
     int it = 0;
     int rc = NOP_OK;
-    for (it = 1; it <= imax; ++it) {
+    if (recast_fused_supported(c)) {
+        const float* const Wl[4] = {Wp(ctx, 0, 0), Wp(ctx, 0, 1), Wp(ctx, 0, 2), Wp(ctx, 0, 3)};
+        const float* const bl[4] = {Bp(ctx, 0, 0), Bp(ctx, 0, 1), Bp(ctx, 0, 2), Bp(ctx, 0, 3)};
+        rc = recast_fused_run(ctx, B, h, predict_only ? 1e300 : tol, imax, PS, PD, u, Wl, bl,
+                              Tref, beta, beta_keep, status, iters, prev, run, active, &it);
+        if (rc != NOP_OK) return rc;
+        it = imax + 1;   // skip the generic loop
+    }
+    int* active_h = nullptr;
+    NOP_CUDA_TRY(ctx, cudaMallocHost(&active_h, sizeof(int)));
+    for (it = it == 0 ? 1 : it; it <= imax; ++it) {
         split_kernel<<<B, 128, 0, ctx->stream>>>(M, h, PS, PD, u, Usp, sig, flags);
         if (cudaGetLastError() != cudaSuccess) { rc = NOP_ECUDA; break; }
         ctx->count_launch(false);

@@ -174,6 +174,14 @@ int recast_update(nop_ctx* ctx, int B, int M, double tol, const float* unew, flo
 int sp_eigen(nop_ctx* ctx, double tol, int itmax, double* phi_d, std::vector<double>* k_h,
              std::vector<int>* status_h, std::vector<int>* iters_h);
 
+// Fused recast iteration for the 128-sensor, 4 x 128, p = 128 DeepONet
+// (recast_fused.cu); active2 points at two device counters.
+bool recast_fused_supported(const nop_no_config& c);
+int recast_fused_run(nop_ctx* ctx, int B, double h, double tol, int itmax, const float* PS,
+                     const float* PD, float* u, const float* const W[4], const float* const b[4],
+                     const float* Tref, float* beta, float* beta_keep, int* status, int* iters,
+                     double* prev, int* run, int* active2, int* its);
+
 // 2D x-y solver (sn2d.cu)
 int xy_solve(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* phi0, double k0,
              double* phi_out, bool out_dev, double* k_out, nop_stats* st);

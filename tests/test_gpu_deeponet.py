@@ -124,10 +124,12 @@ def test_predict_matches_oracle(solver, width, p):
         assert rel_l2(g, ref) < 5e-3
 
 
-def test_recast_matches_oracle(solver):
-    # small last-layer weights make the recast map a contraction for random nets
-    insts = _setup_instances(solver, [120, 64, 300, 511], seed=20)
-    cfg, P = _small(solver, m=128, width=64, p=32, seed=11, scale_last=2e-3)
+@pytest.mark.parametrize("width,p", [(64, 32), (128, 128)])
+def test_recast_matches_oracle(solver, width, p):
+    # small last-layer weights make the recast map a contraction for random
+    # nets; 128 x 128 x depth 4 runs the fused one-launch iteration
+    insts = _setup_instances(solver, [120, 64, 300, 511] + [200] * 17, seed=20)
+    cfg, P = _small(solver, m=128, width=width, p=p, seed=11, scale_last=2e-3)
     phi, info = solver.recast_iterate(tol=1e-5, itmax=100)
     op = R.DeepONetOp(P, 10.0, 128, quant=NN.bf16_round)
     for b, (s, g) in enumerate(zip(insts, split(phi, insts))):
@@ -137,10 +139,11 @@ def test_recast_matches_oracle(solver):
         assert rel_l2(g, ref) < 1e-2
 
 
-def test_recast_divergence_falls_back(solver):
+@pytest.mark.parametrize("width,p", [(64, 32), (128, 128)])
+def test_recast_divergence_falls_back(solver, width, p):
     # an operator with a large output scale makes the recast map expand
     insts = _setup_instances(solver, [100], seed=30)
-    cfg, P = _small(solver, m=128, width=64, p=32, seed=12, scale_last=50.0)
+    cfg, P = _small(solver, m=128, width=width, p=p, seed=12, scale_last=50.0)
     phi, info = solver.recast_iterate(tol=1e-8, itmax=200)
     if info["status"][0] == -5:          # diverged: the prediction is the plain zero guess
         assert np.all(phi == 0)
