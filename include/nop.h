@@ -380,6 +380,12 @@ int nop_set_timing(nop_ctx *ctx, int enable);
  * nop_set_timing(ctx, 1). */
 int nop_get_timing(nop_ctx *ctx, nop_timings *out);
 
+/* Per-instance trace of the last slab solve run with timing on (profiling
+ * aid): start time relative to the first instance, duration (ms), and 1 where
+ * the instance ran on a whole block rather than one warp.  n must be the
+ * batch size; any output pointer may be NULL.  NOP_ESTATE if no such trace. */
+int nop_get_trace(nop_ctx *ctx, int n, double *start_ms, double *duration_ms, int *block_path);
+
 #ifdef __cplusplus
 }
 #endif

@@ -111,6 +111,14 @@ class Solver:
         return {k: getattr(t, k) for k, _ in t._fields_}
 
     # ---------------------------------------------------- neural operator
+    def trace(self):
+        """Per-instance (start ms, duration ms, block path) of the last timed slab solve."""
+        t0, d = np.zeros(self.n_inst), np.zeros(self.n_inst)
+        bp = np.zeros(self.n_inst, dtype=np.int32)
+        self._check(self._L.nop_get_trace(self.h, self.n_inst, t0.ctypes.data, d.ctypes.data,
+                                          bp.ctypes.data), "nop_get_trace")
+        return t0, d, bp
+
     def no_set(self, cfg, params):
         """Install an operator; params: dict of arrays (names of no_param_names)."""
         flat = flatten_params(cfg, params)

@@ -105,6 +105,7 @@ SIGNATURES = {
     "nop_sp_eigen": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_void_p,
                                C.c_void_p, C.POINTER(nop_stats)]),
     "nop_get_timing": (C.c_int, [C.c_void_p, C.POINTER(nop_timings)]),
+    "nop_get_trace": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "nop_solve_eigen": (C.c_int, [C.c_void_p, C.POINTER(nop_solve_opts), C.c_void_p,
                                   C.c_double, C.c_void_p, C.c_void_p,
                                   C.POINTER(nop_stats)]),

@@ -183,6 +183,20 @@ int nop_get_timing(nop_ctx* ctx, nop_timings* out) {
     return NOP_OK;
 }
 
+int nop_get_trace(nop_ctx* ctx, int n, double* start_ms, double* duration_ms, int* block_path) {
+    if (!ctx || n < 0) return NOP_EINVAL;
+    if ((size_t)n * 3 != ctx->trace_inst.size()) {
+        ctx->set_error("no per-instance trace of that size (time a slab solve first)");
+        return NOP_ESTATE;
+    }
+    for (int b = 0; b < n; ++b) {
+        if (start_ms) start_ms[b] = ctx->trace_inst[3 * b];
+        if (duration_ms) duration_ms[b] = ctx->trace_inst[3 * b + 1];
+        if (block_path) block_path[b] = ctx->trace_inst[3 * b + 2] != 0.0;
+    }
+    return NOP_OK;
+}
+
 int nop_set_problem(nop_ctx* ctx, const nop_problem* p) {
     if (!ctx || !p) return NOP_EINVAL;
     NOP_CUDA_TRY(ctx, cudaSetDevice(ctx->device));

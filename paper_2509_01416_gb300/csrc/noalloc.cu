@@ -153,6 +153,7 @@ extern "C" int nop_slab_solve_noalloc(const double* sigma_t, const double* sigma
     a.n_small = 1;
     a.big_list = ints + 0;
     a.n_big = 0;
+    a.big_blocks = 0;
     a.counter = ints + 1;
     a.cell_off = ll + 0;
     a.ncell = ints + 3;

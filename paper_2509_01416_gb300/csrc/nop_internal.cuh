@@ -115,6 +115,7 @@ struct nop_ctx {
     // per-instance trace summary of the last slab solve (timing on)
     double trace_span_ms = 0, trace_max_ms = 0, trace_mean_ms = 0;
     int trace_big = 0;
+    std::vector<double> trace_inst;   // per instance: start ms, duration ms, block path
     // Open a timed phase on the stream; returns the mark index or -1.
     int phase_begin(int phase);
     void phase_end(int mark);

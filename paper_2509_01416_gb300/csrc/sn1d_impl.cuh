@@ -6,6 +6,9 @@
 // GPU organisation.  One warp owns one slab instance at a time and runs its
 // whole iteration (all sweeps, norms, eigenvalue updates) without leaving the
 // kernel; warps pull instances from a work counter in longest-first order.
+// Instances whose latency on one warp would exceed the batch's mean warp
+// load run on a whole 12-warp block instead, their angles split over the
+// warps (one block per SM, 192 KB of staging shared memory).
 // The 32 lanes are split into nt = 32/ng cell chunks x ng angle groups; a lane
 // carries A polar angles |mu| of its group over its chunk, first for mu < 0
 // (right to left) and then for mu > 0 (left to right).  Along the cells the
@@ -27,9 +30,9 @@
 #pragma once
 #include "nop_internal.cuh"
 
-#define SN1D_THREADS 128
-#define SN1D_BLOCKS_PER_SM 3
-#define SN1D_STAGE_BYTES (64 * 1024)
+#define SN1D_THREADS 384
+#define SN1D_BLOCKS_PER_SM 1
+#define SN1D_STAGE_BYTES (192 * 1024)
 
 namespace nop {
 
@@ -50,6 +53,7 @@ struct Sn1dArgs {
     int n_small;
     const int* big_list;     // large instances (one whole block each), longest first
     int n_big;
+    int big_blocks;          // blocks [0, big_blocks) drain the large-instance queue first
     int* counter;            // [0] small queue, [1] big queue
     const long long* cell_off;
     const int* ncell;
@@ -350,19 +354,23 @@ __device__ double si_iteration(const Sn1dArgs& a, const Grp& gr, const Stage<T>&
             const int hi = hb + j * A + q;
             bnd[q] = (a.bc_right && hi < he) ? PB[(g * h + hi) * 2 + 1] : T(0);
         }
-        sweep_half<T, A, true>(gr.block, X, U, sg, I, lg, cc, wt, bnd, out, acc_d, acc_n);
-        __syncwarp();
+        // on the block path a warp without angles (fewer angles than warps)
+        // only joins the barriers
+        if (hb < he) {
+            sweep_half<T, A, true>(gr.block, X, U, sg, I, lg, cc, wt, bnd, out, acc_d, acc_n);
+            __syncwarp();
 #pragma unroll
-        for (int q = 0; q < A; ++q) {
-            const int hi = hb + j * A + q;
-            if (hi < he && (lane >> lg) == 0) PB[(g * h + hi) * 2 + 0] = out[q];
-            bnd[q] = a.bc_left ? out[q] : T(0);
-        }
-        sweep_half<T, A, false>(gr.block, X, U, sg, I, lg, cc, wt, bnd, out, acc_d, acc_n);
+            for (int q = 0; q < A; ++q) {
+                const int hi = hb + j * A + q;
+                if (hi < he && (lane >> lg) == 0) PB[(g * h + hi) * 2 + 0] = out[q];
+                bnd[q] = a.bc_left ? out[q] : T(0);
+            }
+            sweep_half<T, A, false>(gr.block, X, U, sg, I, lg, cc, wt, bnd, out, acc_d, acc_n);
 #pragma unroll
-        for (int q = 0; q < A; ++q) {
-            const int hi = hb + j * A + q;
-            if (hi < he && (lane >> lg) == 0) PB[(g * h + hi) * 2 + 1] = out[q];
+            for (int q = 0; q < A; ++q) {
+                const int hi = hb + j * A + q;
+                if (hi < he && (lane >> lg) == 0) PB[(g * h + hi) * 2 + 1] = out[q];
+            }
         }
         gr.sync();
         if (gr.block) {
@@ -555,9 +563,37 @@ __device__ __forceinline__ void dispatch(const Sn1dArgs& a, const Grp& gr, const
     }
 }
 
-// Persistent kernel: blocks first drain the queue of large instances (the
-// whole block on one instance, its angles split over the warps), then every
-// warp drains the queue of small instances on its own.
+// Large instances run on a whole block (angles split over its warps), small
+// ones on one warp.  Both queues are longest-first work counters.
+template <typename T>
+__device__ void drain_big(const Sn1dArgs& a, double* red, int* job, unsigned char* smem_raw) {
+    // block path: [cells] staged pairs, then one row of partial sums per warp
+    Stage<T> sg;
+    sg.ss = (Cell2<T>*)smem_raw;
+    sg.cells = a.smem_cells;
+    sg.part = (T*)(sg.ss + a.smem_cells);
+    Grp gb;
+    gb.block = true;
+    gb.rank = threadIdx.x;
+    gb.size = blockDim.x;
+    gb.warp = threadIdx.x >> 5;
+    gb.nwarps = blockDim.x >> 5;
+    gb.red = red;
+    for (;;) {
+        if (threadIdx.x == 0) *job = atomicAdd(a.counter + 1, 1);
+        __syncthreads();
+        const int jb = *job;
+        __syncthreads();
+        if (jb >= a.n_big) break;
+        dispatch<T>(a, gb, sg, a.big_list[jb]);
+    }
+    __syncthreads();
+}
+
+// Persistent kernel.  Blocks [0, big_blocks) start on the large queue and
+// then help with the small one; the other blocks start on the small queue
+// (every warp on its own) and then help with what is left of the large one,
+// so both kinds run side by side from the start and the tail is shared.
 template <typename T>
 __global__ void __launch_bounds__(SN1D_THREADS, SN1D_BLOCKS_PER_SM) sn1d_kernel(Sn1dArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -565,29 +601,8 @@ __global__ void __launch_bounds__(SN1D_THREADS, SN1D_BLOCKS_PER_SM) sn1d_kernel(
     __shared__ int job;
     const int lane = threadIdx.x & 31;
     constexpr int nw = SN1D_THREADS / 32;
-    if (a.n_big > 0) {
-        // block path: [cells] staged pairs, then nw rows of partial sums
-        Stage<T> sg;
-        sg.ss = (Cell2<T>*)smem_raw;
-        sg.cells = a.smem_cells;
-        sg.part = (T*)(sg.ss + a.smem_cells);
-        Grp gb;
-        gb.block = true;
-        gb.rank = threadIdx.x;
-        gb.size = blockDim.x;
-        gb.warp = threadIdx.x >> 5;
-        gb.nwarps = blockDim.x >> 5;
-        gb.red = red;
-        for (;;) {
-            if (threadIdx.x == 0) job = atomicAdd(a.counter + 1, 1);
-            __syncthreads();
-            const int jb = job;
-            __syncthreads();
-            if (jb >= a.n_big) break;
-            dispatch<T>(a, gb, sg, a.big_list[jb]);
-        }
-        __syncthreads();
-    }
+    const bool big_first = a.n_big > 0 && (int)blockIdx.x < a.big_blocks;
+    if (big_first) drain_big<T>(a, red, &job, smem_raw);
     // warp path: each warp stages into its own slab
     constexpr int slab = SN1D_STAGE_BYTES / (nw * (int)sizeof(Cell2<T>));
     Grp gw;
@@ -601,7 +616,7 @@ __global__ void __launch_bounds__(SN1D_THREADS, SN1D_BLOCKS_PER_SM) sn1d_kernel(
         int jw = 0;
         if (lane == 0) jw = atomicAdd(a.counter, 1);
         jw = __shfl_sync(0xffffffffu, jw, 0);
-        if (jw >= a.n_small) return;
+        if (jw >= a.n_small) break;
         const int inst = a.order_list[jw];
         Stage<T> sw;
         sw.ss = a.ncell[inst] <= slab
@@ -610,6 +625,10 @@ __global__ void __launch_bounds__(SN1D_THREADS, SN1D_BLOCKS_PER_SM) sn1d_kernel(
         sw.part = nullptr;
         sw.cells = slab;
         dispatch<T>(a, gw, sw, inst);
+    }
+    if (a.n_big > 0 && !big_first) {
+        __syncthreads();
+        drain_big<T>(a, red, &job, smem_raw);
     }
 }
 
@@ -712,11 +731,13 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
     // per iteration of its lane split (4 passes of ceil(I/nt) steps when the
     // cells are chunked, 2 otherwise).  With longest-first scheduling the
     // batch takes about max(mean warp load, longest latency); an instance
-    // whose latency is well above the mean warp load runs on a whole block,
-    // which cuts its latency at the price of the block's other warps.
+    // whose latency is above the mean warp load runs on a whole block (12
+    // warps), which cuts its latency several times at the price of about 1.5x
+    // its SM time on one warp (measured on the 4096-slab batch: thresholds
+    // of 0.5-1.5x the mean load gave 33-34, 28.8 and 30-33 ms).
     std::vector<int> cfg(B), small, big;
     std::vector<double> lat(B);
-    double lat_sum = 0;
+    double lat_sum = 0, big_work = 0, small_work = 0;
     for (int b = 0; b < B; ++b) {
         int lg, A;
         sn1d_pick_config(s.ncell[b], s.order[b], &lg, &A);
@@ -727,13 +748,14 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
         lat_sum += lat[b];
     }
     const double mean_load = lat_sum / warps_total;
+
     int smem_cells = 1;
     for (int b = 0; b < B; ++b) {
         const int h = s.order[b] / 2;
-        const bool fits = h >= SN1D_THREADS / 32 && s.ncell[b] <= max_smem_cells;
+        const bool fits = s.ncell[b] <= max_smem_cells;
         const bool is_big =
             fits && (o->schedule == NOP_SCHED_BLOCK ||
-                     (o->schedule == NOP_SCHED_AUTO && B > 1 && lat[b] > 1.5 * mean_load));
+                     (o->schedule == NOP_SCHED_AUTO && B > 1 && lat[b] > mean_load));
         if (is_big) {
             int lg, A;
             const int hw = (h + SN1D_THREADS / 32 - 1) / (SN1D_THREADS / 32);
@@ -741,10 +763,26 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
             cfg[b] = (lg << 8) | A;
             big.push_back(b);
             smem_cells = std::max(smem_cells, s.ncell[b]);
+            // latency on the block: the same iterations over its lane split
+            const int nt = 32 >> lg;
+            lat[b] = cost[b] / ((double)s.ncell[b] * s.order[b] * G) *
+                     (nt > 1 ? 4.0 : 2.0) * ((s.ncell[b] + nt - 1) / nt) * G;
+            big_work += lat[b];
         } else {
             small.push_back(b);
+            small_work += lat[b] / (SN1D_THREADS / 32);
         }
         cost[b] = lat[b];
+    }
+    // Large and small instances run side by side from the start: a share of
+    // the blocks proportional to the large instances' block-time takes the
+    // large queue first, the other blocks go straight to the small queue.
+    int big_blocks = 0;
+    if (!big.empty()) {
+        const double share = big_work / std::max(1e-30, big_work + small_work);
+        big_blocks = (int)std::ceil(share * blocks_max);
+        big_blocks = std::max(1, std::min<int>(big_blocks, (int)big.size()));
+        if (small.empty()) big_blocks = std::min<int>(blocks_max, (int)big.size());
     }
     auto longest_first = [&](int x, int y) { return cost[x] > cost[y]; };
     std::stable_sort(small.begin(), small.end(), longest_first);
@@ -782,6 +820,7 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
     a.n_small = (int)small.size();
     a.big_list = big_d;
     a.n_big = (int)big.size();
+    a.big_blocks = big_blocks;
     a.smem_cells = smem_cells;
     a.counter = counter;
     a.cell_off = s.cell_off_d;
@@ -862,12 +901,16 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
         NOP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
         unsigned long long t0 = ~0ull, t1 = 0;
         double mx = 0, sum = 0;
+        for (int b = 0; b < B; ++b) t0 = std::min(t0, tr[3 * b]);
+        ctx->trace_inst.assign(3 * (size_t)B, 0.0);
         for (int b = 0; b < B; ++b) {
-            t0 = std::min(t0, tr[3 * b]);
             t1 = std::max(t1, tr[3 * b + 1]);
             const double d = (double)(tr[3 * b + 1] - tr[3 * b]) * 1e-6;
             mx = std::max(mx, d);
             sum += d;
+            ctx->trace_inst[3 * b] = (double)(tr[3 * b] - t0) * 1e-6;
+            ctx->trace_inst[3 * b + 1] = d;
+            ctx->trace_inst[3 * b + 2] = (tr[3 * b + 2] & 0x80000000ull) ? 1.0 : 0.0;
         }
         ctx->trace_span_ms = (double)(t1 - t0) * 1e-6;
         ctx->trace_max_ms = mx;
