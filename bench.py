@@ -34,8 +34,34 @@ UNIT = "solves/s"
 TOL = 1e-6
 RECAST_TOL = 1e-3
 RECAST_ITMAX = 30
+# DRAM bytes (read + write) of one warm-step sweep launch on this workload,
+# from the ncu capture summarised in profiles/sn1d_kernel_4096slab.txt; None
+# once the sweep kernel changes until it is captured again.
+SWEEP_TRAFFIC_BYTES = 252.2e6
 WORKLOAD = ("4096 slabs, cells U{64..2048}, GL S_N N even U{8..64}, sinusoidal or "
             "piecewise coefficients, Fourier sources, vacuum, tol 1e-6 rel. L2 flux change")
+
+
+# ------------------------------------------------------------ multi-rank
+def rank_instances(rank, limit=0):
+    """The rank's own batch: the 4096-slab recipe seeded by the rank (weak
+    scaling; ranks share no instances and exchange no data)."""
+    return W.config5(seed=5 + rank, n_inst=limit if limit > 0 else 4096)
+
+
+def max_over_ranks(x, world, device):
+    """Largest value of x over the ranks (the job's elapsed time)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, steps, seconds):
+    """Units all ranks processed divided by the slowest rank's time."""
+    return world * units_per_rank * steps / seconds
 
 
 def _peaks():
@@ -150,9 +176,7 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    insts = W.config5(seed=5 + rank)
-    if args.instances > 0:
-        insts = insts[:args.instances]
+    insts = rank_instances(rank, args.instances)
     cores = os.cpu_count() or 1
 
     if args.impl == "reference":
@@ -231,17 +255,14 @@ def main():
         barrier()
         tm = s.timing()
         s.set_timing(False)
-        t = torch.tensor([ev0.elapsed_time(ev1)], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item()), tm, info
+        return max_over_ranks(ev0.elapsed_time(ev1), world, "cuda"), tm, info
 
     os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
     clk = Clocks(local, os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % rank))
     plain_ms, plain_tm, plain_info = timed(False, max(1, args.steps // 2))
     ms_max, tm, info = timed(True, args.steps, clk)
-    value = world * B * args.steps / (ms_max / 1e3)
-    plain_value = world * B * max(1, args.steps // 2) / (plain_ms / 1e3)
+    value = whole_job_rate(world, B, args.steps, ms_max / 1e3)
+    plain_value = whole_job_rate(world, B, max(1, args.steps // 2), plain_ms / 1e3)
 
     # ---- end to end through the C ABI with host buffers (warm start)
     h2d = sum(a.nbytes for a in (n, wdt, order, sigt, sigs, src))
@@ -255,10 +276,7 @@ def main():
                                             recast_tol=RECAST_TOL, recast_itmax=RECAST_ITMAX)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * B * args.steps / float(te.item())
+    e2e_value = whole_job_rate(world, B, args.steps, max_over_ranks(e2e_s, world, "cuda"))
 
     if rank != 0:
         s.close()
@@ -325,7 +343,9 @@ def main():
         "gpu_launches": int(tm["launches"]),
         "roofline": {"bound": "alu", "kernel": "sn1d_kernel<float>", "achieved": achieved,
                      "peak": mufu_peak, "unit": "cell-angle updates/s",
-                     "frac": achieved / mufu_peak if mufu_peak else None, "traffic": None,
+                     "frac": achieved / mufu_peak if mufu_peak else None,
+                     "traffic": SWEEP_TRAFFIC_BYTES if B == 4096 else None,
+                     "traffic_unit": "bytes per launch (ncu dram read + write)",
                      "peak_source": "SFU reciprocal rate 16/clk/SM x %d SMs x %.0f MHz "
                                     "(sm_max_mhz, %s)" % (n_sm, smx, src_peak),
                      "sweep_ms_per_step": tm["sweep_ms"] / args.steps,

@@ -1,0 +1,61 @@
+"""The bench's multi-rank path on CPU: two gloo ranks on 127.0.0.1.
+
+Instances are independent, so ranks shard the work (each its own seeded
+batch) and exchange nothing but the MAX of their elapsed times.  This checks
+the sharding (no shared instances), the max-over-ranks reduction that the
+bench's timing uses and the whole-job rate built from it.
+"""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as tmp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import bench
+        insts = bench.rank_instances(rank, limit=6)
+        sig = [(s.I, s.N, float(s.sigt[0]), float(s.Q.sum())) for s in insts]
+        elapsed = 0.5 + rank            # rank 1 is the slow one
+        t = bench.max_over_ranks(elapsed, world, "cpu")
+        rate = bench.whole_job_rate(world, len(insts), 3, t)
+        out[rank] = (sig, t, rate)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.timeout(300)
+def test_two_ranks_shard_and_reduce():
+    world = 2
+    mgr = tmp.Manager()
+    out = mgr.dict()
+    tmp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+    s0, t0, r0 = out[0]
+    s1, t1, r1 = out[1]
+    # every rank sees the slowest rank's time
+    assert t0 == t1 == 1.5
+    # whole-job rate: all ranks' units over the slowest time
+    assert r0 == pytest.approx(world * 6 * 3 / 1.5)
+    # the two shards are different batches
+    assert not set(s0) & set(s1)
+
+
+def test_rank_batches_are_prefix_stable():
+    import bench
+    a = bench.rank_instances(0, limit=5)
+    b = bench.rank_instances(0, limit=9)
+    for x, y in zip(a, b):
+        assert x.I == y.I and x.N == y.N
+        assert np.array_equal(x.sigt, y.sigt) and np.array_equal(x.Q, y.Q)
