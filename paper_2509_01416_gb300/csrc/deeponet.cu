@@ -16,6 +16,7 @@
 // centres.  Converged instances freeze.  The final flux at the instance's own
 // cell centres is beta . trunk(x_c).
 #include <algorithm>
+#include <numeric>
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -368,18 +369,23 @@ __device__ __forceinline__ void ft_mma(float (&c)[4], const uint32_t (&a)[4], ui
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// Every warp owns 32 points (two m16 tiles), so each weight fragment loaded
-// from shared memory feeds two tensor-core instructions.
+// The trunk depends on the cell centre x = (i + 0.5) / I only, so instances
+// with the same cell count I share it: the kernel walks the distinct points
+// (groups of instances with equal I, CSR lists) and writes the inner product
+// with every instance of the group.  Every warp owns 32 points (two m16
+// tiles), so each weight fragment loaded from shared memory feeds two
+// tensor-core instructions.
 __global__ void __launch_bounds__(32 * FT_WARPS) trunk_fused_kernel(
-    long long C, int B, const long long* cell_off, const int* ncell, const float* W1,
-    const float* b1, const float* W2, const float* b2, const float* W3, const float* b3,
-    const float* W4, const float* b4, const float* beta_keep, const int* status, double* phi) {
+    long long P, int NG, const long long* grp_pt_off, const int* grp_I, const int* grp_inst_off,
+    const int* inst_list, const long long* cell_off, const float* W1, const float* b1,
+    const float* W2, const float* b2, const float* W3, const float* b3, const float* W4,
+    const float* b4, const float* beta_keep, const int* status, double* phi) {
     extern __shared__ __align__(16) unsigned char ft_smem[];
     __nv_bfloat16(*Ws)[FT_W][FT_W + FT_PAD] = (__nv_bfloat16(*)[FT_W][FT_W + FT_PAD])ft_smem;
     __nv_bfloat16(*H)[FT_W + FT_PAD] =
         (__nv_bfloat16(*)[FT_W + FT_PAD])(ft_smem + 3 * sizeof(__nv_bfloat16) * FT_W * (FT_W + FT_PAD));
     __shared__ float bs[4][FT_W], w1s[FT_W];
-    __shared__ int pinst[FT_PTS];
+    __shared__ int pgrp[FT_PTS], pidx[FT_PTS];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int gq = lane >> 2, tq = lane & 3;
     for (int e = tid; e < FT_W * FT_W; e += blockDim.x) {
@@ -398,23 +404,25 @@ __global__ void __launch_bounds__(32 * FT_WARPS) trunk_fused_kernel(
     }
     __syncthreads();
     const int r0 = warp * 16 * FT_MT;
-    for (long long t0 = (long long)blockIdx.x * FT_PTS; t0 < C; t0 += (long long)gridDim.x * FT_PTS) {
-        // owning instance and coordinate of the warp's 32 points, one lane each
+    for (long long t0 = (long long)blockIdx.x * FT_PTS; t0 < P; t0 += (long long)gridDim.x * FT_PTS) {
+        // group and coordinate of the warp's 32 points, one lane each
         float xl = 0.f;
         {
             const long long c = t0 + r0 + lane;
-            int b = -1;
-            if (c < C) {
-                int lo = 0, hi = B - 1;
+            int g = -1, i = 0;
+            if (c < P) {
+                int lo = 0, hi = NG - 1;
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
-                    if (cell_off[mid] <= c) lo = mid;
+                    if (grp_pt_off[mid] <= c) lo = mid;
                     else hi = mid - 1;
                 }
-                b = lo;
-                xl = (float)((c - cell_off[lo] + 0.5) / ncell[lo]);
+                g = lo;
+                i = (int)(c - grp_pt_off[lo]);
+                xl = (float)((i + 0.5) / grp_I[lo]);
             }
-            pinst[r0 + lane] = b;
+            pgrp[r0 + lane] = g;
+            pidx[r0 + lane] = i;
         }
         // layer 1 for the warp's points: h = relu(x w1 + b1), BF16
         for (int rr = 0; rr < 16 * FT_MT; ++rr) {
@@ -469,30 +477,44 @@ __global__ void __launch_bounds__(32 * FT_WARPS) trunk_fused_kernel(
                 __syncwarp();
             }
         }
-        // output layer values + bias, inner product with the instance's beta
+        // output layer values + bias (BF16 operands), then the inner product
+        // with the coefficients of every instance of the point's group
+#pragma unroll
+        for (int mt = 0; mt < FT_MT; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 16; ++nt)
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2)
+#pragma unroll
+                    for (int cc = 0; cc < 2; ++cc)
+                        acc[mt][nt][2 * h2 + cc] = __bfloat162float(__float2bfloat16_rn(
+                            acc[mt][nt][2 * h2 + cc] + bs[3][nt * 8 + 2 * tq + cc]));
 #pragma unroll
         for (int mt = 0; mt < FT_MT; ++mt)
 #pragma unroll
             for (int h2 = 0; h2 < 2; ++h2) {
                 const int row = r0 + mt * 16 + gq + 8 * h2;
-                const int b = pinst[row];
-                float d = 0.f;
-                if (b >= 0 && (!status || status[b] != 3)) {
+                const int g = pgrp[row], i = pidx[row];
+                const int k0 = g >= 0 ? grp_inst_off[g] : 0;
+                const int nk = g >= 0 ? grp_inst_off[g + 1] - k0 : 0;
+                int kmax = nk;   // warp-uniform trip count for the shuffles
+                for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+                for (int k = 0; k < kmax; ++k) {
+                    const int b = k < nk ? inst_list[k0 + k] : -1;
+                    float d = 0.f;
+                    if (b >= 0 && (!status || status[b] != 3)) {
+                        const float* be = beta_keep + (long long)b * FT_W;
 #pragma unroll
-                    for (int nt = 0; nt < 16; ++nt)
+                        for (int nt = 0; nt < 16; ++nt)
 #pragma unroll
-                        for (int cc = 0; cc < 2; ++cc) {
-                            const int n = nt * 8 + 2 * tq + cc;
-                            const float tv = acc[mt][nt][2 * h2 + cc] + bs[3][n];
-                            d += __bfloat162float(__float2bfloat16_rn(tv)) *
-                                 __bfloat162float(
-                                     __float2bfloat16_rn(beta_keep[(long long)b * FT_W + n]));
-                        }
+                            for (int cc = 0; cc < 2; ++cc)
+                                d += acc[mt][nt][2 * h2 + cc] *
+                                     __bfloat162float(__float2bfloat16_rn(be[nt * 8 + 2 * tq + cc]));
+                    }
+                    d += __shfl_xor_sync(0xffffffffu, d, 1);
+                    d += __shfl_xor_sync(0xffffffffu, d, 2);
+                    if (tq == 0 && b >= 0) phi[cell_off[b] + i] = d;
                 }
-                d += __shfl_xor_sync(0xffffffffu, d, 1);
-                d += __shfl_xor_sync(0xffffffffu, d, 2);
-                const long long c = t0 + row;
-                if (tq == 0 && c < C) phi[c] = d;
             }
         __syncwarp();
     }
@@ -721,12 +743,43 @@ int deeponet_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* sta
         NOP_CUDA_TRY(ctx, cudaFuncSetAttribute(trunk_fused_kernel,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem));
+        // instances grouped by cell count (CSR): distinct points once
+        std::vector<int> order(B);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int x, int y) { return s.ncell[x] < s.ncell[y]; });
+        std::vector<long long> gpt(1, 0);
+        std::vector<int> gI, ginst(1, 0);
+        for (int k = 0; k < B; ++k) {
+            const int I = s.ncell[order[k]];
+            if (gI.empty() || gI.back() != I) {
+                if (!gI.empty()) ginst.push_back(k);
+                gI.push_back(I);
+                gpt.push_back(gpt.back() + I);
+            }
+        }
+        ginst.push_back(B);
+        const int NG = (int)gI.size();
+        const long long P = gpt.back();
+        NOP_TRY(ctx->scratch("ft_gpt", sizeof(long long) * (NG + 1), &q));
+        long long* gpt_d = (long long*)q;
+        NOP_TRY(ctx->scratch("ft_gint", sizeof(int) * (2 * (size_t)NG + 1 + B), &q));
+        int* gI_d = (int*)q;
+        int* ginst_d = gI_d + NG;
+        int* list_d = ginst_d + NG + 1;
+        std::vector<int> ints(gI);
+        ints.insert(ints.end(), ginst.begin(), ginst.end());
+        ints.insert(ints.end(), order.begin(), order.end());
+        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(gpt_d, gpt.data(), sizeof(long long) * (NG + 1),
+                                          cudaMemcpyHostToDevice, ctx->stream));
+        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(gI_d, ints.data(), sizeof(int) * ints.size(),
+                                          cudaMemcpyHostToDevice, ctx->stream));
         const int grid = (int)std::max<long long>(
-            1, std::min<long long>((C + FT_PTS - 1) / FT_PTS, ctx->sm_count));
+            1, std::min<long long>((P + FT_PTS - 1) / FT_PTS, ctx->sm_count));
         trunk_fused_kernel<<<grid, 32 * FT_WARPS, smem, ctx->stream>>>(
-            C, B, s.cell_off_d, s.ncell_d, Wp(ctx, 1, 0), Bp(ctx, 1, 0), Wp(ctx, 1, 1),
-            Bp(ctx, 1, 1), Wp(ctx, 1, 2), Bp(ctx, 1, 2), Wp(ctx, 1, 3), Bp(ctx, 1, 3), beta_keep,
-            status, phi_d);
+            P, NG, gpt_d, gI_d, ginst_d, list_d, s.cell_off_d, Wp(ctx, 1, 0), Bp(ctx, 1, 0),
+            Wp(ctx, 1, 1), Bp(ctx, 1, 1), Wp(ctx, 1, 2), Bp(ctx, 1, 2), Wp(ctx, 1, 3),
+            Bp(ctx, 1, 3), beta_keep, status, phi_d);
         NOP_CUDA_TRY(ctx, cudaGetLastError());
         ctx->count_launch(false);
         ctx->phase_end(mk);
