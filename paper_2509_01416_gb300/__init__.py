@@ -250,6 +250,15 @@ class Solver:
         return mu[:k], eta[:k], w[:k]
 
     # ------------------------------------------------------------ solves
+    def _out(self, out):
+        if out is None:
+            return np.zeros(self.G * self.C)
+        if (not isinstance(out, np.ndarray) or out.dtype != np.float64 or
+                not out.flags.c_contiguous or out.size != self.G * self.C):
+            raise ValueError("out must be a contiguous float64 array of %d entries"
+                             % (self.G * self.C))
+        return out
+
     def _stats(self):
         st = capi.nop_stats()
         it = np.zeros(self.n_inst, dtype=np.int32)
@@ -257,9 +266,11 @@ class Solver:
         st.inst_iterations, st.inst_status = capi._ptr(it, capi._ip), capi._ptr(ss, capi._ip)
         return st, it, ss
 
-    def solve_fixed_source(self, phi0=None, check=True, **kw):
+    def solve_fixed_source(self, phi0=None, check=True, out=None, **kw):
+        """Fixed-source solve; out: optional float64 host array of G*C entries
+        (for instance a pinned buffer) that receives the flux."""
         o = _opts(**kw)
-        phi = np.zeros(self.G * self.C)
+        phi = self._out(out)
         p0 = None if phi0 is None else capi._f64(phi0)
         st, it, ss = self._stats()
         rc = self._L.nop_solve_fixed_source(self.h, C.byref(o),
@@ -284,9 +295,9 @@ class Solver:
         return {"rc": rc, "iterations": it, "status": ss,
                 "recast_iterations": st.recast_iterations, "recast_status": st.recast_status}
 
-    def solve_eigen(self, phi0=None, k0=0.0, check=True, **kw):
+    def solve_eigen(self, phi0=None, k0=0.0, check=True, out=None, **kw):
         o = _opts(**kw)
-        phi = np.zeros(self.G * self.C)
+        phi = self._out(out)
         k = np.zeros(self.n_inst)
         p0 = None if phi0 is None else capi._f64(phi0)
         st, it, ss = self._stats()

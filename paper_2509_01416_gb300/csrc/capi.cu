@@ -74,15 +74,46 @@ int upload(nop_ctx* ctx, const char* name, const void* src, size_t bytes, void**
     return NOP_OK;
 }
 
-bool finite_pos(const double* a, long long n) {
-    for (long long i = 0; i < n; ++i)
-        if (!(a[i] > 0.0) || !std::isfinite(a[i])) return false;
-    return true;
-}
 bool finite_all(const double* a, long long n) {
     for (long long i = 0; i < n; ++i)
         if (!std::isfinite(a[i])) return false;
     return true;
+}
+
+// Coefficient check on the device: flag = 1 if a sigma_t is not a positive
+// finite number or any other coefficient is not finite.
+__global__ void check_kernel(long long nt, const double* sigt, long long ns, const double* sigs,
+                             long long nq, const double* src, long long nf, const double* nsf,
+                             int* flag) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    bool bad = false;
+    for (long long i = i0; i < nt; i += stride) bad |= !(sigt[i] > 0.0) || !isfinite(sigt[i]);
+    for (long long i = i0; i < ns; i += stride) bad |= !isfinite(sigs[i]);
+    for (long long i = i0; i < nq; i += stride) bad |= !isfinite(src[i]);
+    for (long long i = i0; i < nf; i += stride) bad |= !isfinite(nsf[i]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+// Largest in-group scattering ratio sigma_s(g->g) / sigma_t(g) of each slab
+// instance (one block per instance); feeds the scheduler's iteration guess.
+__global__ void cmax_kernel(int G, long long C, const long long* cell_off, const int* ncell,
+                            const double* sigt, const double* sigs, double* cmax) {
+    __shared__ double red[32];
+    const int b = blockIdx.x;
+    double m = 0.0;
+    for (int g = 0; g < G; ++g)
+        for (long long i = threadIdx.x; i < ncell[b]; i += blockDim.x) {
+            const long long c = cell_off[b] + i;
+            m = fmax(m, sigs[((long long)g * G + g) * C + c] / sigt[(long long)g * C + c]);
+        }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+        cmax[b] = fmax(m, red[0]);
+    }
 }
 
 }  // namespace
@@ -247,11 +278,8 @@ int nop_set_problem(nop_ctx* ctx, const nop_problem* p) {
             ctx->set_error("boundary condition must be vacuum or reflective");
             return NOP_EINVAL;
         }
-    if (!finite_pos(p->sigma_t, (long long)G * C) ||
-        !finite_all(p->sigma_s, (long long)G * G * C) ||
-        (fixed && !finite_all(p->source, (long long)G * C)) ||
-        (fiss && !finite_all(p->nu_sigma_f, (long long)G * C))) {
-        ctx->set_error("coefficients must be finite and sigma_t > 0");
+    if (fiss && !finite_all(p->chi, G)) {
+        ctx->set_error("chi must be finite");
         return NOP_EINVAL;
     }
     ctx->geometry = p->geometry;
@@ -278,6 +306,23 @@ int nop_set_problem(nop_ctx* ctx, const nop_problem* p) {
         NOP_TRY(upload(ctx, "chi", p->chi, sizeof(double) * G, &d));
         ctx->chi_d = (double*)d;
     }
+    // the coefficients are checked on the device, where they now are
+    NOP_TRY(ctx->scratch("chk_flag", sizeof(int), &d));
+    int* flag_d = (int*)d;
+    NOP_CUDA_TRY(ctx, cudaMemsetAsync(flag_d, 0, sizeof(int), ctx->stream));
+    {
+        const long long n = (long long)G * G * C;
+        const int grid = (int)std::max<long long>(
+            1, std::min<long long>((n + 255) / 256, 8LL * ctx->sm_count));
+        check_kernel<<<grid, 256, 0, ctx->stream>>>(
+            (long long)G * C, ctx->sigt_d, (long long)G * G * C, ctx->sigs_d,
+            fixed ? (long long)G * C : 0, ctx->src_d, fiss ? (long long)G * C : 0, ctx->nsf_d,
+            flag_d);
+        NOP_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    int bad = 0;
+    NOP_CUDA_TRY(ctx, cudaMemcpyAsync(&bad, flag_d, sizeof(int), cudaMemcpyDeviceToHost,
+                                      ctx->stream));
     if (p->geometry == NOP_GEOM_SLAB) {
         nop::SlabDev& s = ctx->slab;
         const int B = p->n_inst;
@@ -304,14 +349,6 @@ int nop_set_problem(nop_ctx* ctx, const nop_problem* p) {
             bo += (long long)G * s.order[b];
         }
         s.bnd_total = bo;
-        s.cmax.assign(B, 0.0);
-        for (int b = 0; b < B; ++b)
-            for (int g = 0; g < G; ++g)
-                for (long long c = s.cell_off[b]; c < s.cell_off[b] + s.ncell[b]; ++c) {
-                    const double r = p->sigma_s[((long long)g * G + g) * C + c] /
-                                     p->sigma_t[(long long)g * C + c];
-                    s.cmax[b] = std::max(s.cmax[b], r);
-                }
         NOP_TRY(upload(ctx, "cell_off", s.cell_off.data(), sizeof(long long) * B, &d));
         s.cell_off_d = (long long*)d;
         NOP_TRY(upload(ctx, "ncell", s.ncell.data(), sizeof(int) * B, &d));
@@ -324,6 +361,14 @@ int nop_set_problem(nop_ctx* ctx, const nop_problem* p) {
         s.width_d = (double*)d;
         NOP_TRY(upload(ctx, "boff", boff.data(), sizeof(long long) * B, &d));
         s.boff_d = (long long*)d;
+        NOP_TRY(ctx->scratch("cmax", sizeof(double) * B, &d));
+        double* cmax_d = (double*)d;
+        cmax_kernel<<<B, 128, 0, ctx->stream>>>(G, C, s.cell_off_d, s.ncell_d, ctx->sigt_d,
+                                                ctx->sigs_d, cmax_d);
+        NOP_CUDA_TRY(ctx, cudaGetLastError());
+        s.cmax.assign(B, 0.0);
+        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(s.cmax.data(), cmax_d, sizeof(double) * B,
+                                          cudaMemcpyDeviceToHost, ctx->stream));
         NOP_TRY(nop::build_gauss_legendre(ctx));   // synchronises the stream
     } else {
         ctx->xy.nx = p->nx;
@@ -331,7 +376,11 @@ int nop_set_problem(nop_ctx* ctx, const nop_problem* p) {
         ctx->xy.lx = p->lx;
         ctx->xy.ly = p->ly;
         NOP_TRY(nop::build_level_symmetric_s8(ctx));
-        NOP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    NOP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (bad) {
+        ctx->set_error("coefficients must be finite and sigma_t > 0");
+        return NOP_EINVAL;
     }
     ctx->has_problem = true;
     return NOP_OK;

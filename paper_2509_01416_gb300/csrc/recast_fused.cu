@@ -121,6 +121,13 @@ __global__ void __launch_bounds__(RF_THREADS, 1) recast_fused_kernel(RfArgs a) {
     const int gq = lane >> 2, tq = lane & 3, n0 = 16 * warp;
     const int ntiles = (a.B + RF_NI - 1) / RF_NI;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        // a tile whose instances are all frozen (converged, capped or
+        // diverged) has nothing to do
+        {
+            const int b = tile * RF_NI + (tid & (RF_NI - 1));
+            const int running = tid < RF_NI && b < a.B && a.status[b] == 0;
+            if (!__syncthreads_or(running)) continue;
+        }
         // 1. recast source S + D u of two instances per warp, split into parts
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
