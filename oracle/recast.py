@@ -13,7 +13,8 @@ started from phi_0 = 0 (so phi_1 = N[S]).  The result seeds the model-based
 solver (Eq. 9a/10b, Eq. 20).  For eigenproblems the simple preconditioning of
 App. A2 (Eq. A5) replaces the inner solve by one recast operator application
 per outer iteration, and its (k, phi) seed the model-based power iteration
-(Eq. A6).
+(Eq. A6); the constrained preconditioning (Eq. A7-A8) follows every operator
+prediction by one model-based source iteration.
 
 Readings where the paper is silent (the CUDA side does the same):
   * the operator acts on its own grid.  DeepONet: M uniform bins over the
@@ -256,6 +257,62 @@ def sp_eigen(prob, apply_group, p_star, tol_k=1e-6, tol_phi=1e-6, itmax=2000):
         dk = abs(k_new - k) / abs(k_new)
         dphi = T.rel_change(new, phi)
         k, phi = k_new, new
+        if dk <= tol_k and dphi <= tol_phi:
+            status = OK
+            break
+    return k, phi, n, status
+
+
+def cp_eigen(prob, apply_group, p_star, quad, tol_k=1e-6, tol_phi=1e-6, itmax=2000):
+    """Constrained preconditioning, App. A2 Eq. A7-A8.
+
+    Every outer step first predicts with the operator exactly as the simple
+    preconditioning does (Eq. A7: groups in order, newest in-scatter, recast
+    mismatch delta_g phi_g), then refines the prediction with one application
+    of the model-based iteration operator M (Eq. A8): one source iteration
+    (a transport sweep per group, Gauss-Seidel over groups) started from the
+    prediction, whose fission source chi F / k is built from the prediction
+    with the current k.  The outer update P then sets k <- k P and scales the
+    flux to unit production.  Returns (k, phi, outer iterations, status).
+    """
+    sigt_s, sigs_s = p_star
+    G = prob.G
+    sw = T.make_sweeper(prob, quad)
+    phi = np.ones_like(prob.sigt)
+    phi /= T.production(prob, phi)
+    k = 1.0
+    status = NOCONV
+    n = 0
+    shape = (G,) + (1,) * (prob.sigt.ndim - 1)
+    for n in range(1, itmax + 1):
+        # Eq. A7: the operator's prediction u^(n+1/4)
+        F = np.sum(prob.nusigf * phi, axis=0)
+        quarter = phi.copy()
+        for g in range(G):
+            src = prob.chi[g] * F / k
+            for gp in range(G):
+                if gp != g:
+                    src = src + prob.sigs[gp, g] * quarter[gp]
+            delta = (prob.sigs[g, g] - sigs_s) - (prob.sigt[g] - sigt_s)
+            quarter[g] = apply_group((src + delta * phi[g])[None])[0]
+        if not np.all(np.isfinite(quarter)):
+            status = DIVERGED
+            break
+        # Eq. A8: one model-based source iteration from the prediction
+        Fq = np.sum(prob.nusigf * quarter, axis=0)
+        srcq = prob.chi.reshape(shape) * Fq[None] / k
+        half = T.source_iteration(prob, quad, src=srcq, phi0=quarter, tol=0.0, itmax=1,
+                                  sweeper=sw).phi
+        Pn = T.production(prob, half)
+        if not np.isfinite(Pn) or Pn == 0:
+            status = DIVERGED
+            break
+        k_new = k * Pn
+        half = half / Pn
+        sw.scale(1.0 / Pn)
+        dk = abs(k_new - k) / abs(k_new)
+        dphi = T.rel_change(half, phi)
+        k, phi = k_new, half
         if dk <= tol_k and dphi <= tol_phi:
             status = OK
             break

@@ -108,3 +108,42 @@ def test_sp_eigen_with_exact_operator_at_p_star():
     assert st == R.OK
     assert abs(k - e.k) < 1e-9
     assert np.max(np.abs(phi - e.phi)) < 1e-7 * np.max(e.phi)
+
+
+def test_cp_eigen_with_exact_operator_at_p_star():
+    # App. A2 Eq. A7-A8: with the exact operator at p = p* the true eigenpair
+    # is a fixed point of the constrained step (the prediction reproduces it
+    # and one source iteration leaves it unchanged), so CP reaches the
+    # model-based k and flux
+    I, L = 40, 10.0
+    quad = Qd.gauss_legendre(8)
+    x = (np.arange(I) + 0.5) * L / I
+    nsf = 0.5 + 0.4 * np.sin(np.pi * x / L)
+    P = T.uniform_slab(I, L, P_STAR[0], P_STAR[1], nusigf=nsf)
+    k, phi, n, st = R.cp_eigen(P, _exact_star_apply(I, L, quad), P_STAR, quad,
+                               tol_k=1e-11, tol_phi=1e-9)
+    e = T.power_iteration(P, quad, tol_k=1e-12, tol_phi=1e-10, tol_inner=1e-13)
+    assert st == R.OK
+    assert abs(k - e.k) < 1e-9
+    assert np.max(np.abs(phi - e.phi)) < 1e-7 * np.max(e.phi)
+
+
+def test_cp_refinement_is_one_model_iteration():
+    # with an operator that returns its input unchanged the prediction is the
+    # recast source itself; the constrained step must then equal one source
+    # iteration from that prediction with its own fission source.  A CP step
+    # that skipped the refinement, or refined from phi^n instead, fails.
+    I, L = 30, 10.0
+    quad = Qd.gauss_legendre(8)
+    x = (np.arange(I) + 0.5) * L / I
+    P = T.uniform_slab(I, L, 1.0 + 0.2 * np.cos(x), 0.4 + 0.1 * np.sin(x), nusigf=0.6)
+    ident = lambda S: np.array(S, float)
+    k1, phi1, n, st = R.cp_eigen(P, ident, P_STAR, quad, tol_k=0.0, tol_phi=0.0, itmax=1)
+    phi0 = np.ones((1, I)) / T.production(P, np.ones((1, I)))
+    delta = (P.sigs[0, 0] - P_STAR[1]) - (P.sigt[0] - P_STAR[0])
+    quarter = (P.nusigf[0] * phi0[0] * 1.0 + delta * phi0[0])[None]
+    src = P.nusigf * quarter
+    half = T.source_iteration(P, quad, src=src, phi0=quarter, tol=0.0, itmax=1).phi
+    Pn = T.production(P, half)
+    assert abs(k1 - Pn) < 1e-12
+    assert np.max(np.abs(phi1 - half / Pn)) < 1e-12 * np.max(np.abs(half / Pn))
