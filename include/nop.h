@@ -61,9 +61,12 @@ extern "C" {
 
 #define NOP_WARM_NONE    0 /* plain guess: zero flux (fixed source), flat flux and k=1 (eigen) */
 #define NOP_WARM_RECAST  1 /* neural-operator recast warm start (needs a network) */
+#define NOP_WARM_RECAST_CP 2 /* eigen only: constrained preconditioning (App. A2
+                                Eq. A7-A8) as the warm start; vacuum faces    */
 
 /* flags of nop_solve_opts.flags */
 #define NOP_PHI0_DEVICE  1 /* phi0 is a device pointer                        */
+#define NOP_SP_CONSTRAINED 4 /* nop_sp_eigen: the constrained variant (Eq. A7-A8) */
 #define NOP_OUT_DEVICE   2 /* phi_out / k_out are device pointers; the call does
                               not synchronise (results valid once the context
                               stream reaches this point)                      */
@@ -201,7 +204,8 @@ int nop_solve_fixed_source(nop_ctx *ctx, const nop_solve_opts *opts,
  * k_{n+1} = k_n * production(phi_{n+1/2}).
  * phi0 / k0: initial guess (phi0 NULL: flat flux; k0 <= 0: 1.0); with
  *            NOP_WARM_RECAST the simple-preconditioning prediction (App. A2
- *            Eq. A5) replaces both (Eq. A6).
+ *            Eq. A5) replaces both (Eq. A6); with NOP_WARM_RECAST_CP the
+ *            constrained-preconditioning result (Eq. A7-A8) does.
  * k_out:     [n_inst] eigenvalues.
  * Errors: as nop_solve_fixed_source. */
 int nop_solve_eigen(nop_ctx *ctx, const nop_solve_opts *opts, const double *phi0,
@@ -317,7 +321,13 @@ int nop_recast_iterate(nop_ctx *ctx, double tol, int itmax, int flags, double *p
  * went non-finite get the plain guess (flat flux, k = 1) and NOP_EDIVERGE.
  * stats: recast_iterations (max outer steps), recast_status, inst_status,
  * inst_iterations.  Nothing of the problem is modified.  The result seeds
- * nop_solve_eigen with warm_start = NOP_WARM_RECAST (Eq. A6). */
+ * nop_solve_eigen with warm_start = NOP_WARM_RECAST (Eq. A6).
+ *
+ * With NOP_SP_CONSTRAINED in flags, the constrained preconditioning of App.
+ * A2 Eq. A7-A8: every outer step refines the operator's prediction by one
+ * model-based source iteration (a sweep per group, FP32) started from the
+ * prediction, with the fission source chi F / k built from the prediction,
+ * before the outer update.  Vacuum faces only (NOP_EINVAL otherwise). */
 int nop_sp_eigen(nop_ctx *ctx, double tol, int itmax, int flags, double *phi_out,
                  double *k_out, nop_stats *stats);
 

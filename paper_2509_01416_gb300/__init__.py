@@ -310,12 +310,14 @@ class Solver:
                         "recast_iterations": st.recast_iterations,
                         "recast_status": st.recast_status}
 
-    def sp_eigen(self, tol=1e-4, itmax=200):
-        """Simple-preconditioning eigen warm start alone: (k per instance, phi, info)."""
+    def sp_eigen(self, tol=1e-4, itmax=200, constrained=False):
+        """Eigen warm start alone (simple preconditioning, or the constrained
+        variant): (k per instance, phi, info)."""
         phi = np.zeros(self.G * self.C)
         k = np.zeros(self.n_inst)
         st, it, ss = self._stats()
-        self._check(self._L.nop_sp_eigen(self.h, tol, itmax, 0, phi.ctypes.data, k.ctypes.data,
-                                         C.byref(st)), "nop_sp_eigen")
+        flags = capi.NOP_SP_CONSTRAINED if constrained else 0
+        self._check(self._L.nop_sp_eigen(self.h, tol, itmax, flags, phi.ctypes.data,
+                                         k.ctypes.data, C.byref(st)), "nop_sp_eigen")
         return k, phi, {"iterations": it, "status": ss, "max_iterations": st.recast_iterations,
                         "recast_status": st.recast_status}

@@ -489,9 +489,9 @@ int nop_solve_eigen(nop_ctx* ctx, const nop_solve_opts* o, const double* phi0, d
     const int B = ctx->geometry == NOP_GEOM_SLAB ? ctx->slab.n_inst : 1;
     std::vector<double> k0v(B, k0 > 0 ? k0 : 1.0);
     bool phi0_dev = (o->flags & NOP_PHI0_DEVICE) != 0;
-    if (o->warm_start == NOP_WARM_RECAST) {
-        // App. A2: the simple-preconditioning result (Eq. A5) seeds the
-        // model-based power iteration (Eq. A6)
+    if (o->warm_start == NOP_WARM_RECAST || o->warm_start == NOP_WARM_RECAST_CP) {
+        // App. A2: the simple- (Eq. A5) or constrained-preconditioning
+        // (Eq. A7-A8) result seeds the model-based power iteration (Eq. A6)
         if (!ctx->no.loaded) {
             ctx->set_error("warm start requested but no neural operator is loaded");
             return NOP_ESTATE;
@@ -501,7 +501,7 @@ int nop_solve_eigen(nop_ctx* ctx, const nop_solve_opts* o, const double* phi0, d
         std::vector<int> sst, sit;
         NOP_TRY(nop::sp_eigen(ctx, o->recast_tol > 0 ? o->recast_tol : 1e-4,
                               o->recast_itmax > 0 ? o->recast_itmax : 200, (double*)p, &k0v, &sst,
-                              &sit));
+                              &sit, o->warm_start == NOP_WARM_RECAST_CP));
         phi0 = (const double*)p;
         phi0_dev = true;
         if (st) {

@@ -354,7 +354,7 @@ int nop_sp_eigen(nop_ctx* ctx, double tol, int itmax, int flags, double* phi_out
     }
     std::vector<double> k;
     std::vector<int> status, iters;
-    NOP_TRY(sp_eigen(ctx, tol, itmax, pd, &k, &status, &iters));
+    NOP_TRY(sp_eigen(ctx, tol, itmax, pd, &k, &status, &iters, (flags & NOP_SP_CONSTRAINED) != 0));
     if (!(flags & NOP_OUT_DEVICE)) {
         NOP_CUDA_TRY(ctx, cudaMemcpyAsync(phi_out, pd, sizeof(double) * GC, cudaMemcpyDeviceToHost,
                                           ctx->stream));

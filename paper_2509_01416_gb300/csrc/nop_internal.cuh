@@ -172,8 +172,10 @@ int recast_update(nop_ctx* ctx, int B, int M, double tol, const float* unew, flo
 // Simple-preconditioning eigen warm start (sp_eigen.cu): phi_d [G*C] device
 // out (unit production), k/status/iterations per instance on the host.
 // status: 0 cap reached, 1 converged, 3 diverged (phi flat, k = 1).
+// constrained: refine each prediction by one model-based source iteration
+// (App. A2 Eq. A7-A8).
 int sp_eigen(nop_ctx* ctx, double tol, int itmax, double* phi_d, std::vector<double>* k_h,
-             std::vector<int>* status_h, std::vector<int>* iters_h);
+             std::vector<int>* status_h, std::vector<int>* iters_h, bool constrained = false);
 
 // Fused recast iteration for the 128-sensor, 4 x 128, p = 128 DeepONet
 // (recast_fused.cu); active2 points at two device counters.

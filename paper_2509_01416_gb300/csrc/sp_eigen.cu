@@ -144,6 +144,18 @@ __global__ void sp_update_kernel(int G, long long C, const long long* cell_off, 
     }
 }
 
+// fission source of the refinement step: chi_g F_c / k of the cell's instance
+__global__ void fission_source_kernel(int G, long long C, const int* inst, const double* chi,
+                                      const double* F, const double* k, double* src) {
+    const long long n = (long long)G * C;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int g = (int)(e / C);
+        const long long c = e - (long long)g * C;
+        src[e] = chi[g] * F[c] / k[inst[c]];
+    }
+}
+
 // diverged instances restart from the plain guess (flat flux, k = 1)
 __global__ void fallback_kernel(int G, long long C, const int* inst, const int* status, double* phi,
                                 double* k) {
@@ -158,8 +170,34 @@ __global__ void fallback_kernel(int G, long long C, const int* inst, const int* 
 
 }  // namespace
 
+namespace {
+
+// Eq. A8: one model-based source iteration from u (device [G*C]) with the
+// fixed source src (device [G*C]) into out; the solver's own schedule cache
+// is left as it was.
+int refine_once(nop_ctx* ctx, const double* u, const double* src, double* out) {
+    nop_solve_opts o{};
+    o.tol = 1e-300;
+    o.itmax = 1;
+    o.precision = NOP_PREC_F32;
+    o.flags = NOP_PHI0_DEVICE | NOP_OUT_DEVICE;
+    double* keep_src = ctx->src_d;
+    ctx->src_d = const_cast<double*>(src);
+    std::vector<int> keep_iters = ctx->slab.last_iters;
+    int rc;
+    if (ctx->geometry == NOP_GEOM_SLAB)
+        rc = sn1d_solve(ctx, &o, false, u, true, nullptr, out, true, nullptr, nullptr);
+    else
+        rc = xy_solve(ctx, &o, false, u, 0.0, out, true, nullptr, nullptr);
+    ctx->src_d = keep_src;
+    ctx->slab.last_iters = keep_iters;
+    return rc == NOP_ENOCONV ? NOP_OK : rc;   // one iteration is the cap by design
+}
+
+}  // namespace
+
 int sp_eigen(nop_ctx* ctx, double tol, int itmax, double* phi_d, std::vector<double>* k_h,
-             std::vector<int>* status_h, std::vector<int>* iters_h) {
+             std::vector<int>* status_h, std::vector<int>* iters_h, bool constrained) {
     if (!ctx->no.loaded) {
         ctx->set_error("the eigen warm start needs a neural operator");
         return NOP_ESTATE;
@@ -169,6 +207,12 @@ int sp_eigen(nop_ctx* ctx, double tol, int itmax, double* phi_d, std::vector<dou
         return NOP_ESTATE;
     }
     const bool slab = ctx->geometry == NOP_GEOM_SLAB;
+    if (constrained)
+        for (int f = 0; f < (slab ? 2 : 4); ++f)
+            if (ctx->bc[f] != NOP_BC_VACUUM) {
+                ctx->set_error("the constrained eigen warm start needs vacuum faces");
+                return NOP_EINVAL;
+            }
     const int B = slab ? ctx->slab.n_inst : 1;
     const int G = ctx->G;
     const long long C = ctx->C, GC = (long long)G * C;
@@ -181,6 +225,13 @@ int sp_eigen(nop_ctx* ctx, double tol, int itmax, double* phi_d, std::vector<dou
     double* src = (double*)p;
     NOP_TRY(ctx->scratch("sp_inst", sizeof(int) * C, &p));
     int* inst = (int*)p;
+    double *cp_src = nullptr, *cp_half = nullptr;
+    if (constrained) {
+        NOP_TRY(ctx->scratch("cp_src", sizeof(double) * GC, &p));
+        cp_src = (double*)p;
+        NOP_TRY(ctx->scratch("cp_half", sizeof(double) * GC, &p));
+        cp_half = (double*)p;
+    }
     NOP_TRY(ctx->scratch("sp_dbl", sizeof(double) * 3 * (size_t)B, &p));
     double* k = (double*)p;
     double* P = k + B;
@@ -238,12 +289,26 @@ int sp_eigen(nop_ctx* ctx, double tol, int itmax, double* phi_d, std::vector<dou
                                        src);
         }
         if (rc != NOP_OK) break;
-        production_kernel<<<B, 256, 0, ctx->stream>>>(G, C, cell_off, ncell, vol, ctx->nsf_d, nw, P);
+        const double* upd = nw;
+        if (constrained) {
+            // Eq. A8: one source iteration from the prediction, its own
+            // fission source with the current k
+            fission_kernel<<<grid_of(C), 256, 0, ctx->stream>>>(G, C, ctx->nsf_d, nw, F);
+            fission_source_kernel<<<grid_of(GC), 256, 0, ctx->stream>>>(G, C, inst, ctx->chi_d, F,
+                                                                        k, cp_src);
+            if (cudaGetLastError() != cudaSuccess) {
+                rc = NOP_ECUDA;
+                break;
+            }
+            if ((rc = refine_once(ctx, nw, cp_src, cp_half)) != NOP_OK) break;
+            upd = cp_half;
+        }
+        production_kernel<<<B, 256, 0, ctx->stream>>>(G, C, cell_off, ncell, vol, ctx->nsf_d, upd, P);
         if (cudaMemsetAsync(active, 0, sizeof(int), ctx->stream) != cudaSuccess) {
             rc = NOP_ECUDA;
             break;
         }
-        sp_update_kernel<<<B, 256, 0, ctx->stream>>>(G, C, cell_off, ncell, tol, P, nw, phi_d, k,
+        sp_update_kernel<<<B, 256, 0, ctx->stream>>>(G, C, cell_off, ncell, tol, P, upd, phi_d, k,
                                                      status, iters, active);
         if (cudaGetLastError() != cudaSuccess) {
             rc = NOP_ECUDA;

@@ -147,3 +147,89 @@ def test_sp_two_group_2d_matches_oracle(solver):
     kr, pr, n, status = R.sp_eigen(prob, op, W.P_STAR, tol_k=1e-30, tol_phi=1e-30, itmax=2)
     assert abs(k[0] - kr) < 1e-2 * abs(kr), (k[0], kr)
     assert rel_l2(phi, pr.reshape(-1)) < 2e-2
+
+
+# ------------------------------------------------ constrained preconditioning
+def test_cp_outer_steps_match_oracle(solver, fno1d):
+    """App. A2 Eq. A7-A8: prediction, one model source iteration, outer update;
+    three outer steps against the oracle (FP32 refinement sweep on the GPU)."""
+    from oracle import quadrature as Qd
+    cfg, P = fno1d
+    solver.no_set(cfg, P)
+    insts = _eigen_slabs(400)
+    _set(solver, insts)
+    k, phi, info = solver.sp_eigen(tol=1e-30, itmax=3, constrained=True)
+    op = R.FNOOp1D(P, W.L_SLAB, quant=NN.bf16_round)
+    for b, (s, g) in enumerate(zip(insts, split(phi, insts))):
+        kr, pr, n, st = R.cp_eigen(oracle_slab(s), op, W.P_STAR, Qd.gauss_legendre(s.N),
+                                   tol_k=1e-30, tol_phi=1e-30, itmax=3)
+        assert n == 3 and int(info["iterations"][b]) == 3
+        assert abs(k[b] - kr) < 5e-3 * abs(kr), (k[b], kr)
+        assert rel_l2(g, pr[0]) < 1e-2
+
+
+def test_cp_lands_closer_than_sp(solver, fno1d):
+    # the refinement step enforces the transport equation every outer step,
+    # so the constrained fixed point is nearer the eigenpair than the simple one
+    cfg, P = fno1d
+    solver.no_set(cfg, P)
+    insts = _eigen_slabs(500)
+    _set(solver, insts)
+    kp, php, _ = solver.solve_eigen(tol=1e-6, tol_k=1e-8, tol_inner=1e-6, itmax=2000)
+    ks, phs, _ = solver.sp_eigen(tol=1e-3, itmax=300)
+    kc, phc, ic = solver.sp_eigen(tol=1e-3, itmax=300, constrained=True)
+    assert ic["recast_status"] == 0, ic
+    assert np.all(np.abs(kc - kp) <= np.abs(ks - kp) + 1e-4), (kc, ks, kp)
+
+
+def test_cp_warm_start_keeps_the_eigenpair(solver, fno1d):
+    cfg, P = fno1d
+    solver.no_set(cfg, P)
+    insts = _eigen_slabs(600)
+    _set(solver, insts)
+    kw = dict(tol=1e-7, tol_k=1e-9, tol_inner=1e-7, itmax=5000)
+    kp, php, ip = solver.solve_eigen(**kw)
+    kc, phc, ic = solver.solve_eigen(warm_start=2, recast_tol=1e-3, recast_itmax=100, **kw)
+    assert ic["recast_iterations"] > 0
+    assert np.all(np.abs(kc - kp) < 1e-6), (kc, kp)
+    assert rel_l2(phc, php) < 1e-5
+    assert int(ic["inner"].sum()) < int(ip["inner"].sum()), (ic["inner"], ip["inner"])
+
+
+def test_cp_needs_vacuum_faces(solver, fno1d):
+    from paper_2509_01416_gb300 import NopError
+    cfg, P = fno1d
+    solver.no_set(cfg, P)
+    insts = _eigen_slabs(700)
+    n, wdt, order, sigt, sigs, _, nsf = slab_batch_arrays(insts)
+    solver.set_slabs(n, wdt, order, sigt, sigs, nu_sigma_f=nsf, chi=np.ones(1), bc=(1, 0))
+    with pytest.raises(NopError):
+        solver.sp_eigen(tol=1e-3, itmax=5, constrained=True)
+
+
+def test_cp_two_group_2d_matches_oracle(solver):
+    from oracle import quadrature as Qd
+    from paper_2509_01416_gb300 import NOP_NO_FNO2D, no_config
+    nx, ny, G = 24, 16, 2
+    rng = np.random.default_rng(9)
+    st = np.stack([rng.uniform(0.6, 0.9, (ny, nx)), rng.uniform(1.0, 1.4, (ny, nx))])
+    S = np.zeros((G, G, ny, nx))
+    S[0, 0] = 0.5 * st[0]
+    S[0, 1] = 0.2 * st[0]
+    S[1, 1] = 0.6 * st[1]
+    S[1, 0] = 0.05 * st[1]
+    nsf = np.stack([0.1 * st[0], 0.4 * st[1]])
+    chi = np.array([1.0, 0.0])
+    solver.set_xy(nx, ny, 10.0, 10.0, st.reshape(-1), S.reshape(-1), nu_sigma_f=nsf.reshape(-1),
+                  chi=chi)
+    cfg = no_config(NOP_NO_FNO2D, width=8, modes=4, depth=4, proj=16, length=10.0)
+    P = W.fno2d_init(3, width=8, modes=4, proj=16)
+    solver.no_set(cfg, P)
+    k, phi, info = solver.sp_eigen(tol=1e-30, itmax=2, constrained=True)
+    prob = T.XY(dx=10.0 / nx, dy=10.0 / ny, sigt=st, sigs=S, nusigf=nsf, chi=chi,
+                bc={f: T.VACUUM for f in ("x0", "xL", "y0", "yL")})
+    op = R.FNOOp2D(P, 10.0, 10.0, quant=NN.bf16_round)
+    kr, pr, n, status = R.cp_eigen(prob, op, W.P_STAR, Qd.level_symmetric_s8(), tol_k=1e-30,
+                                   tol_phi=1e-30, itmax=2)
+    assert abs(k[0] - kr) < 1e-2 * abs(kr), (k[0], kr)
+    assert rel_l2(phi, pr.reshape(-1)) < 2e-2
