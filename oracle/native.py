@@ -35,6 +35,9 @@ def lib():
         L.ora_sweep1d.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_int, dp, dp,
                                   dp, dp, dp, dp, dp]
         L.ora_sweep1d.restype = None
+        L.ora_sweep1d_p1.argtypes = [ctypes.c_int, dp, dp, dp, dp, ctypes.c_int, dp, dp,
+                                     dp, dp, dp, dp, dp, dp]
+        L.ora_sweep1d_p1.restype = None
         L.ora_sweep2d.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                   ctypes.c_double, dp, dp, ctypes.c_int, dp, dp, dp,
                                   dp, dp, dp, dp, dp, dp]
@@ -66,6 +69,21 @@ def sweep1d(dx, sigt, q, mu, w, in_left, in_right):
     lib().ora_sweep1d(I, _p(dx), _p(sigt), _p(q), N, _p(mu), _p(w),
                       _p(in_left), _p(in_right), _p(phi), _p(out_l), _p(out_r))
     return phi, out_l, out_r
+
+
+def sweep1d_p1(dx, sigt, q0, q1, mu, w, in_left, in_right):
+    """DD sweep with emission q0 + mu q1 per direction (Eq. 25).  Returns
+    (phi, current, out_left, out_right)."""
+    dx, sigt, q0, q1, mu, w = map(_f64, (dx, sigt, q0, q1, mu, w))
+    in_left, in_right = _f64(in_left), _f64(in_right)
+    I, N = sigt.shape[0], mu.shape[0]
+    phi = np.zeros(I)
+    cur = np.zeros(I)
+    out_l = np.zeros(N)
+    out_r = np.zeros(N)
+    lib().ora_sweep1d_p1(I, _p(dx), _p(sigt), _p(q0), _p(q1), N, _p(mu), _p(w),
+                         _p(in_left), _p(in_right), _p(phi), _p(cur), _p(out_l), _p(out_r))
+    return phi, cur, out_l, out_r
 
 
 def sweep2d(dx, dy, sigt, q, mu, eta, w, in_x, in_y):

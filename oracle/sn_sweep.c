@@ -70,6 +70,48 @@ void ora_sweep1d(int I, const double *dx, const double *sigt, const double *q,
     }
 }
 
+/* 1D sweep with a linearly anisotropic emission (Sec. 5.1 Eq. 25): the
+ * emission of direction n in cell i is q0[i] + mu[n] q1[i].  Same arguments
+ * as ora_sweep1d plus
+ *   cur[I]           out: sum_n w[n] mu[n] psi_n,i (the current)
+ */
+void ora_sweep1d_p1(int I, const double *dx, const double *sigt, const double *q0,
+                    const double *q1, int N, const double *mu, const double *w,
+                    const double *in_left, const double *in_right,
+                    double *phi, double *cur, double *out_left, double *out_right)
+{
+    for (int i = 0; i < I; ++i) {
+        phi[i] = 0.0;
+        cur[i] = 0.0;
+    }
+    for (int n = 0; n < N; ++n) {
+        double m = mu[n];
+        if (m > 0.0) {
+            double psi_in = in_left[n];
+            for (int i = 0; i < I; ++i) {
+                double a = m / dx[i];
+                double q = q0[i] + m * q1[i];
+                double psi_c = (q + 2.0 * a * psi_in) / (sigt[i] + 2.0 * a);
+                phi[i] += w[n] * psi_c;
+                cur[i] += w[n] * m * psi_c;
+                psi_in = 2.0 * psi_c - psi_in;
+            }
+            out_right[n] = psi_in;
+        } else {
+            double psi_in = in_right[n];
+            for (int i = I - 1; i >= 0; --i) {
+                double a = -m / dx[i];
+                double q = q0[i] + m * q1[i];
+                double psi_c = (q + 2.0 * a * psi_in) / (sigt[i] + 2.0 * a);
+                phi[i] += w[n] * psi_c;
+                cur[i] += w[n] * m * psi_c;
+                psi_in = 2.0 * psi_c - psi_in;
+            }
+            out_left[n] = psi_in;
+        }
+    }
+}
+
 /* 2D x-y sweep on a uniform nx x ny mesh, cell (i, j) stored at [j*nx + i].
  *   sigt, q          [ny*nx]
  *   M                directions; mu[M], eta[M] (both nonzero), w[M]

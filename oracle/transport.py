@@ -10,7 +10,10 @@ Follows the paper's model-based solver:
     iteration M with the fission source frozen, and an outer update P that
     recomputes k from the production rate and renormalises the flux;
   * multigroup, Sec. 5.3 Eq. 27-29: group-to-group scattering and the
-    chi-weighted fission source enter each group's equation as sources.
+    chi-weighted fission source enter each group's equation as sources;
+  * linearly anisotropic in-group scattering, Sec. 5.1 Eq. 25 (1D fixed
+    source): the emission of direction mu adds (3/2) Sigma_s1 mu J, with the
+    current J = sum w mu psi of the previous source iteration (zero at first).
 
 Readings where the paper is silent (identical on the CUDA side):
   * spatial scheme: diamond difference, no negative-flux fix-up;
@@ -49,6 +52,9 @@ class Slab:
     chi: Optional[np.ndarray] = None     # (G,) fission spectrum
     bc_left: str = VACUUM
     bc_right: str = VACUUM
+    # (G, I) first Legendre moment of the in-group scattering, Sec. 5.1 Eq. 25
+    # (linearly anisotropic emission); None: isotropic scattering
+    sigs1: Optional[np.ndarray] = None
 
     @property
     def G(self):
@@ -82,13 +88,15 @@ class XY:
 
 
 def uniform_slab(I, L, sigt, sigs, Q=None, nusigf=None, chi=None,
-                 bc_left=VACUUM, bc_right=VACUUM):
+                 bc_left=VACUUM, bc_right=VACUUM, sigs1=None):
     """Slab of I equal cells over width L; scalar or per-cell coefficients, 1 group."""
     one = np.ones(I)
     P = Slab(dx=np.full(I, L / I),
              sigt=(np.asarray(sigt, float) * one)[None, :],
              sigs=(np.asarray(sigs, float) * one)[None, None, :],
              bc_left=bc_left, bc_right=bc_right)
+    if sigs1 is not None:
+        P.sigs1 = (np.asarray(sigs1, float) * one)[None, :]
     if Q is not None:
         P.Q = (np.asarray(Q, float) * one)[None, :]
     if nusigf is not None:
@@ -139,6 +147,24 @@ class _Sweeper1D:
                                          in_l, np.zeros(len(pos)))
         self.out_right[g][pos] = out_r
         return phi_n + phi_p
+
+    def sweep_p1(self, g, q0, q1):
+        """Sweep with the emission q0 + mu q1 of Eq. 25; returns (phi, current)."""
+        p, mu, w = self.p, self.mu, self.w
+        neg, pos, mir = self.neg, self.pos, self.mir
+        in_r = np.zeros(len(neg))
+        if p.bc_right == REFLECTIVE:
+            in_r = self.out_right[g][mir[neg]]
+        phi_n, cur_n, out_l, _ = native.sweep1d_p1(p.dx, p.sigt[g], q0, q1, mu[neg], w[neg],
+                                                   np.zeros(len(neg)), in_r)
+        self.out_left[g][neg] = out_l
+        in_l = np.zeros(len(pos))
+        if p.bc_left == REFLECTIVE:
+            in_l = self.out_left[g][mir[pos]]
+        phi_p, cur_p, _, out_r = native.sweep1d_p1(p.dx, p.sigt[g], q0, q1, mu[pos], w[pos],
+                                                   in_l, np.zeros(len(pos)))
+        self.out_right[g][pos] = out_r
+        return phi_n + phi_p, cur_n + cur_p
 
     def scale(self, s):
         self.out_left *= s
@@ -224,6 +250,10 @@ def source_iteration(prob, quad, src=None, phi0=None, tol=1e-10, itmax=100000,
     G = prob.G
     sw = make_sweeper(prob, quad) if sweeper is None else sweeper
     phi = np.zeros_like(prob.sigt) if phi0 is None else np.array(phi0, float)
+    # Eq. 25: the linearly anisotropic part of the emission, (3/2) Sigma_s1 mu J,
+    # with the current J of the previous iteration (zero at the start)
+    aniso = isinstance(prob, Slab) and prob.sigs1 is not None
+    cur = np.zeros_like(phi) if aniso else None
     hist = []
     change = np.inf
     it = 0
@@ -234,7 +264,10 @@ def source_iteration(prob, quad, src=None, phi0=None, tol=1e-10, itmax=100000,
             for gp in range(G):
                 scat = scat + prob.sigs[gp, g] * phi[gp]
             q = sw.emission(scat + (S[g] if S is not None else 0.0))
-            phi[g] = sw.sweep(g, q)
+            if aniso:
+                phi[g], cur[g] = sw.sweep_p1(g, q, 1.5 * prob.sigs1[g] * cur[g])
+            else:
+                phi[g] = sw.sweep(g, q)
         change = rel_change(phi, old)
         if history:
             hist.append(change)
@@ -267,6 +300,8 @@ def power_iteration(prob, quad, tol_k=1e-10, tol_phi=1e-10, tol_inner=1e-10,
     to unit production.
     """
     G = prob.G
+    if isinstance(prob, Slab) and prob.sigs1 is not None:
+        raise ValueError("anisotropic scattering is modelled for fixed-source problems only")
     sw = make_sweeper(prob, quad)
     phi = np.ones_like(prob.sigt) if phi0 is None else np.array(phi0, float)
     P0 = production(prob, phi)
