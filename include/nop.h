@@ -94,6 +94,13 @@ typedef struct nop_ctx nop_ctx;
  *   chi       [G]        fission spectrum (NULL for fixed source)
  * Boundary conditions: bc[0..1] = slab left/right (applied to every
  *   instance); bc[0..3] = x=0, x=lx, y=0, y=ly for x-y.
+ * Linearly anisotropic scattering (Sec. 5.1 Eq. 25), slab fixed-source
+ *   problems only (NULL otherwise):
+ *   sigma_s1  [G*C]      first Legendre moment of the in-group scattering;
+ *                        the emission of direction mu adds (3/2) sigma_s1 mu J
+ *                        with the current J of the previous source iteration.
+ *                        The recast warm start ignores it (Sec. 5.1: the
+ *                        operator only knows isotropic scattering).
  */
 typedef struct {
     int geometry;
@@ -110,6 +117,7 @@ typedef struct {
     const double *nu_sigma_f;
     const double *chi;
     int bc[4];
+    const double *sigma_s1;  /* slab fixed source only, may be NULL */
 } nop_problem;
 
 /* Solver options.  Convergence is the relative L2 change of the scalar flux

@@ -205,8 +205,9 @@ class Solver:
 
     # ---------------------------------------------------------- problems
     def set_slabs(self, n_cells, width, order, sigma_t, sigma_s, source=None,
-                  nu_sigma_f=None, chi=None, bc=(0, 0)):
-        """Batch of slabs; arrays group-major over all cells (see nop.h)."""
+                  nu_sigma_f=None, chi=None, bc=(0, 0), sigma_s1=None):
+        """Batch of slabs; arrays group-major over all cells (see nop.h).
+        sigma_s1: in-group first Legendre moment (fixed source only)."""
         n_cells = np.ascontiguousarray(n_cells, dtype=np.int32)
         order = np.ascontiguousarray(order, dtype=np.int32)
         width = capi._f64(width)
@@ -221,6 +222,8 @@ class Solver:
         p.n_groups = G
         p.sigma_t, p.sigma_s, p.source, p.nu_sigma_f, p.chi = [capi._ptr(a) for a in arrs]
         p.bc[0], p.bc[1] = int(bc[0]), int(bc[1])
+        s1 = None if sigma_s1 is None else capi._f64(sigma_s1)
+        p.sigma_s1 = capi._ptr(s1)
         self._check(self._L.nop_set_problem(self.h, C.byref(p)), "nop_set_problem")
         self.n_inst, self.G, self.C = len(n_cells), G, int(n_cells.sum())
 

@@ -31,7 +31,8 @@ class nop_problem(C.Structure):
                 ("width", _dp), ("order", _ip), ("nx", C.c_int), ("ny", C.c_int),
                 ("lx", C.c_double), ("ly", C.c_double), ("n_groups", C.c_int),
                 ("sigma_t", _dp), ("sigma_s", _dp), ("source", _dp),
-                ("nu_sigma_f", _dp), ("chi", _dp), ("bc", C.c_int * 4)]
+                ("nu_sigma_f", _dp), ("chi", _dp), ("bc", C.c_int * 4),
+                ("sigma_s1", _dp)]
 
 
 class nop_solve_opts(C.Structure):

@@ -278,6 +278,10 @@ int nop_set_problem(nop_ctx* ctx, const nop_problem* p) {
             ctx->set_error("boundary condition must be vacuum or reflective");
             return NOP_EINVAL;
         }
+    if (p->sigma_s1 && (p->geometry != NOP_GEOM_SLAB || !fixed || fiss)) {
+        ctx->set_error("sigma_s1 is supported for fixed-source slab problems only");
+        return NOP_EINVAL;
+    }
     if (fiss && !finite_all(p->chi, G)) {
         ctx->set_error("chi must be finite");
         return NOP_EINVAL;
@@ -296,6 +300,11 @@ int nop_set_problem(nop_ctx* ctx, const nop_problem* p) {
     ctx->src_d = nullptr;
     ctx->nsf_d = nullptr;
     ctx->chi_d = nullptr;
+    ctx->sigs1_d = nullptr;
+    if (p->sigma_s1) {
+        NOP_TRY(upload(ctx, "sigs1", p->sigma_s1, sizeof(double) * G * C, &d));
+        ctx->sigs1_d = (double*)d;
+    }
     if (fixed) {
         NOP_TRY(upload(ctx, "src", p->source, sizeof(double) * G * C, &d));
         ctx->src_d = (double*)d;
@@ -318,6 +327,10 @@ int nop_set_problem(nop_ctx* ctx, const nop_problem* p) {
             (long long)G * C, ctx->sigt_d, (long long)G * G * C, ctx->sigs_d,
             fixed ? (long long)G * C : 0, ctx->src_d, fiss ? (long long)G * C : 0, ctx->nsf_d,
             flag_d);
+        if (ctx->sigs1_d)
+            check_kernel<<<grid, 256, 0, ctx->stream>>>(0, nullptr, (long long)G * C,
+                                                        ctx->sigs1_d, 0, nullptr, 0, nullptr,
+                                                        flag_d);
         NOP_CUDA_TRY(ctx, cudaGetLastError());
     }
     int bad = 0;

@@ -99,7 +99,7 @@ struct nop_ctx {
     nop::NoState no;
     // FP64 originals
     double *sigt_d = nullptr, *sigs_d = nullptr, *src_d = nullptr, *nsf_d = nullptr,
-           *chi_d = nullptr;
+           *chi_d = nullptr, *sigs1_d = nullptr;
 
     // phase timing (nop_set_timing)
     bool timing = false;

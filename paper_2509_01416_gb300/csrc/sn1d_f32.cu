@@ -18,7 +18,7 @@ int sn1d_launch_f32(const Sn1dArgs& a, long long C, const double* sigt, const do
         return NOP_ECUDA;
     const int pb = (int)std::max<long long>(1, std::min<long long>((C + 255) / 256, 1024));
     sn1d_prepare<float><<<pb, 256, 0, stream>>>(C, 1, sigt, sigs, src, nullptr, nullptr, 0, X,
-                                                nullptr, ext, nullptr);
+                                                nullptr, ext, nullptr, nullptr, nullptr, nullptr);
     sn1d_kernel<float><<<1, SN1D_THREADS, SN1D_STAGE_BYTES, stream>>>(a);
     sn1d_finish<float><<<pb, 256, 0, stream>>>(C, X, phi_out);
     return cudaGetLastError() == cudaSuccess ? NOP_OK : NOP_ECUDA;

@@ -69,6 +69,12 @@ struct Sn1dArgs {
     const void* scat;     // T [G][G][C], halved; only read when G > 1
     void* ext;            // T [G][C], halved external / fission source
     void* psib;           // T boundary fluxes [boff + (g*h + hi)*2 + side]
+    // linearly anisotropic in-group scattering (Eq. 25), fixed source, warp path
+    int p1;
+    const void* y1;       // T [G][C]: (3/2) Sigma_s1
+    void* cur;            // T [G][C]: current J = sum w mu psi of the last iteration
+    void* s1buf;          // T [C]: (3/2) Sigma_s1 J of the group being swept
+    void* jm;             // T [C]: mu < 0 part of the new current
     int bc_left, bc_right;
     int smem_cells;       // cells the block path can stage in shared memory
     // eigen
@@ -164,6 +170,18 @@ struct CSum {
     __device__ __forceinline__ T val() const { return hi + lo; }
 };
 
+// Linearly anisotropic emission (Eq. 25) of one group: the emission of
+// direction mu is s + mu s1, s1 = (3/2) Sigma_s1 J per cell; the sweep also
+// accumulates the new current J = sum w mu psi.
+template <typename T, int A>
+struct P1Op {
+    const T* s1;      // [I] s1 of the cells
+    T* jm;            // [I] mu < 0 part of the current (written by the MINUS half)
+    T* jc;            // [I] the new current (written by the PLUS half)
+    T mua[A];         // |mu| of the lane's angles
+    T wmu[A];         // w |mu|
+};
+
 // One direction half (MINUS: mu < 0, cells right to left) of one group, for
 // the angles this warp carries.  Lanes: nt = 32/ng cell chunks x ng angle
 // groups, A angles per lane.  Diamond difference in increment form: with
@@ -178,12 +196,12 @@ struct CSum {
 // and the squared flux (FP32 per lane within one iteration: the change of an
 // FP32 flux is exact, and the FP64 sum across lanes forms the norms).  Block
 // path: owners add their partial sums to the warp's row.
-template <typename T, int A, bool MINUS>
+template <typename T, int A, bool MINUS, bool P1>
 __device__ __forceinline__ void sweep_half(const bool block, Cell4<T>* X, Cell2<T>* U,
                                            const Stage<T>& sg, int I, int lg,
                                            const T (&cc)[A], const T (&wt)[A],
                                            const T (&psi_bnd)[A], T (&psi_out)[A],
-                                           T& acc_d, T& acc_n) {
+                                           T& acc_d, T& acc_n, const P1Op<T, A>& an) {
     const int lane = threadIdx.x & 31;
     const int ng = 1 << lg, nt = 32 >> lg;
     const int j = lane & (ng - 1), t = lane >> lg;
@@ -213,11 +231,15 @@ __device__ __forceinline__ void sweep_half(const bool block, Cell4<T>* X, Cell2<
                 st = v.st;
                 s = MINUS ? (v.y * v.phi + v.z) : U[i].s0;
             }
+            T s1 = T(0);
+            if constexpr (P1) s1 = an.s1[i];
 #pragma unroll
             for (int q = 0; q < A; ++q) {
+                T sq = s;
+                if constexpr (P1) sq = MINUS ? s - an.mua[q] * s1 : s + an.mua[q] * s1;
                 const T r2 = T(2) * rcp_dd(cc[q] + st);
                 D[q] = (r2 * st) * (T(1) - D[q]) + D[q];
-                Bc[q].add(r2 * (s - st * Bc[q].hi));
+                Bc[q].add(r2 * (sq - st * Bc[q].hi));
             }
         }
         // inclusive scan of the chunk maps along the sweep (lanes stride ng)
@@ -253,7 +275,7 @@ __device__ __forceinline__ void sweep_half(const bool block, Cell4<T>* X, Cell2<
     for (int k = 0; k < m; ++k) {
         const bool valid = k < len;
         const int i = MINUS ? (I - 1 - (k0 + k)) : (k0 + k);
-        T p = T(0), s = T(0), phio = T(0), pmv = T(0);
+        T p = T(0), s = T(0), phio = T(0), pmv = T(0), pj = T(0);
         if (valid) {
             T st;
             if (sg.ss) {
@@ -272,14 +294,22 @@ __device__ __forceinline__ void sweep_half(const bool block, Cell4<T>* X, Cell2<
                 s = MINUS ? (v.y * v.phi + v.z) : U[i].s0;
                 if (!MINUS) pmv = U[i].s1;
             }
+            T s1 = T(0);
+            if constexpr (P1) s1 = an.s1[i];
 #pragma unroll
             for (int q = 0; q < A; ++q) {
-                const T dl = rcp_dd(cc[q] + st) * (s - st * psi[q].hi);
-                p += wt[q] * (psi[q].hi + (dl + psi[q].lo));
+                T sq = s;
+                if constexpr (P1) sq = MINUS ? s - an.mua[q] * s1 : s + an.mua[q] * s1;
+                const T dl = rcp_dd(cc[q] + st) * (sq - st * psi[q].hi);
+                const T pc = psi[q].hi + (dl + psi[q].lo);
+                p += wt[q] * pc;
+                if constexpr (P1) pj += (MINUS ? -an.wmu[q] : an.wmu[q]) * pc;
                 psi[q].add(dl + dl);
             }
         }
         for (int o = 1; o < ng; o <<= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+        if constexpr (P1)
+            for (int o = 1; o < ng; o <<= 1) pj += __shfl_xor_sync(0xffffffffu, pj, o);
         if (valid && (k & (ng - 1)) == j) {
             if (block) {
                 sg.part[(threadIdx.x >> 5) * sg.cells + i] += p;
@@ -288,12 +318,14 @@ __device__ __forceinline__ void sweep_half(const bool block, Cell4<T>* X, Cell2<
                 u.s0 = s;
                 u.s1 = p;
                 U[i] = u;
+                if constexpr (P1) an.jm[i] = pj;
             } else {
                 const T phin = p + pmv;
                 const T df = phin - phio;
                 acc_d += df * df;
                 acc_n += phin * phin;
                 X[i].phi = phin;
+                if constexpr (P1) an.jc[i] = pj + an.jm[i];
             }
         }
     }
@@ -320,10 +352,10 @@ __device__ void group_source(const Sn1dArgs& a, const Grp& gr, long long off, in
 // One source iteration over all groups; returns the relative L2 change.
 // [hb, he): this warp's slice of the half-angle range (all of it on the warp
 // path).
-template <typename T, int A>
+template <typename T, int A, bool P1>
 __device__ double si_iteration(const Sn1dArgs& a, const Grp& gr, const Stage<T>& sg, int inst,
                                long long off, int I, int h, int hb, int he, int lg,
-                               const T (&cc)[A], const T (&wt)[A]) {
+                               const T (&cc)[A], const T (&wt)[A], P1Op<T, A>& an) {
     const int lane = threadIdx.x & 31;
     const int j = lane & ((1 << lg) - 1);
     T* PB = (T*)a.psib + a.boff[inst];
@@ -335,6 +367,16 @@ __device__ double si_iteration(const Sn1dArgs& a, const Grp& gr, const Stage<T>&
         }
         Cell4<T>* X = (Cell4<T>*)a.X + (long long)g * a.C + off;
         Cell2<T>* U = (Cell2<T>*)a.U + off;
+        if constexpr (P1) {
+            // s1 = (3/2) Sigma_s1 J from the current of the previous iteration
+            const T* Y1 = (const T*)a.y1 + (long long)g * a.C + off;
+            T* S1 = (T*)a.s1buf + off;
+            an.jc = (T*)a.cur + (long long)g * a.C + off;
+            an.s1 = S1;
+            an.jm = (T*)a.jm + off;
+            for (int i = gr.rank; i < I; i += gr.size) S1[i] = Y1[i] * an.jc[i];
+            gr.sync();
+        }
         if (sg.ss) {
             for (int i = gr.rank; i < I; i += gr.size) {
                 const Cell4<T> v = X[i];
@@ -357,7 +399,8 @@ __device__ double si_iteration(const Sn1dArgs& a, const Grp& gr, const Stage<T>&
         // on the block path a warp without angles (fewer angles than warps)
         // only joins the barriers
         if (hb < he) {
-            sweep_half<T, A, true>(gr.block, X, U, sg, I, lg, cc, wt, bnd, out, acc_d, acc_n);
+            sweep_half<T, A, true, P1>(gr.block, X, U, sg, I, lg, cc, wt, bnd, out, acc_d, acc_n,
+                                       an);
             __syncwarp();
 #pragma unroll
             for (int q = 0; q < A; ++q) {
@@ -365,7 +408,8 @@ __device__ double si_iteration(const Sn1dArgs& a, const Grp& gr, const Stage<T>&
                 if (hi < he && (lane >> lg) == 0) PB[(g * h + hi) * 2 + 0] = out[q];
                 bnd[q] = a.bc_left ? out[q] : T(0);
             }
-            sweep_half<T, A, false>(gr.block, X, U, sg, I, lg, cc, wt, bnd, out, acc_d, acc_n);
+            sweep_half<T, A, false, P1>(gr.block, X, U, sg, I, lg, cc, wt, bnd, out, acc_d, acc_n,
+                                        an);
 #pragma unroll
             for (int q = 0; q < A; ++q) {
                 const int hi = hb + j * A + q;
@@ -404,7 +448,7 @@ __device__ double production(const Sn1dArgs& a, const Grp& gr, long long off, in
     return gr.sum(acc) * dx;
 }
 
-template <typename T, int A>
+template <typename T, int A, bool P1>
 __device__ void solve_instance(const Sn1dArgs& a, const Grp& gr, const Stage<T>& sg, int inst,
                                int lg) {
     const int lane = threadIdx.x & 31;
@@ -422,15 +466,20 @@ __device__ void solve_instance(const Sn1dArgs& a, const Grp& gr, const Stage<T>&
     unsigned long long t_start = 0;
     if (a.trace && gr.rank == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
     T cc[A], wt[A];
+    P1Op<T, A> an{};
 #pragma unroll
     for (int q = 0; q < A; ++q) {
         const int hi = hb + j * A + q;
         if (hi < he) {
             cc[q] = (T)(2.0 * a.mu[q0 + h + hi] / dxv);
             wt[q] = (T)a.w[q0 + h + hi];
+            an.mua[q] = (T)a.mu[q0 + h + hi];
+            an.wmu[q] = (T)(a.w[q0 + h + hi] * a.mu[q0 + h + hi]);
         } else {
             cc[q] = T(1);
             wt[q] = T(0);
+            an.mua[q] = T(0);
+            an.wmu[q] = T(0);
         }
     }
     T* PB = (T*)a.psib + a.boff[inst];
@@ -443,7 +492,7 @@ __device__ void solve_instance(const Sn1dArgs& a, const Grp& gr, const Stage<T>&
     double k = 0.0, dphi = INFINITY;
     if (!a.eigen) {
         for (its = 1; its <= a.itmax; ++its) {
-            change = si_iteration<T, A>(a, gr, sg, inst, off, I, h, hb, he, lg, cc, wt);
+            change = si_iteration<T, A, P1>(a, gr, sg, inst, off, I, h, hb, he, lg, cc, wt, an);
             if (!isfinite(change)) {
                 status = NOP_ENAN;
                 break;
@@ -490,7 +539,8 @@ __device__ void solve_instance(const Sn1dArgs& a, const Grp& gr, const Stage<T>&
             gr.sync();
             int it;
             for (it = 1; it <= a.itmax_inner; ++it) {
-                change = si_iteration<T, A>(a, gr, sg, inst, off, I, h, hb, he, lg, cc, wt);
+                change = si_iteration<T, A, P1>(a, gr, sg, inst, off, I, h, hb, he, lg, cc, wt,
+                                                an);
                 if (!isfinite(change)) {
                     status = NOP_ENAN;
                     break;
@@ -557,9 +607,18 @@ __device__ __forceinline__ void dispatch(const Sn1dArgs& a, const Grp& gr, const
     const int cfg = a.cfg[inst];
     const int A = cfg & 0xff, lg = cfg >> 8;
     switch (A) {
-        case 1: solve_instance<T, 1>(a, gr, sg, inst, lg); break;
-        case 2: solve_instance<T, 2>(a, gr, sg, inst, lg); break;
-        default: solve_instance<T, 4>(a, gr, sg, inst, lg); break;
+        case 1:
+            if (a.p1 && !gr.block) solve_instance<T, 1, true>(a, gr, sg, inst, lg);
+            else solve_instance<T, 1, false>(a, gr, sg, inst, lg);
+            break;
+        case 2:
+            if (a.p1 && !gr.block) solve_instance<T, 2, true>(a, gr, sg, inst, lg);
+            else solve_instance<T, 2, false>(a, gr, sg, inst, lg);
+            break;
+        default:
+            if (a.p1 && !gr.block) solve_instance<T, 4, true>(a, gr, sg, inst, lg);
+            else solve_instance<T, 4, false>(a, gr, sg, inst, lg);
+            break;
     }
 }
 
@@ -636,7 +695,8 @@ __global__ void __launch_bounds__(SN1D_THREADS, SN1D_BLOCKS_PER_SM) sn1d_kernel(
 template <typename T>
 __global__ void sn1d_prepare(long long C, int G, const double* sigt, const double* sigs,
                              const double* src, const double* nsf, const double* phi0,
-                             int phi0_flat, Cell4<T>* X, T* scat, T* ext, T* nsfT) {
+                             int phi0_flat, Cell4<T>* X, T* scat, T* ext, T* nsfT,
+                             const double* sigs1, T* y1, T* cur) {
     const long long total = (long long)G * C;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
@@ -651,6 +711,10 @@ __global__ void sn1d_prepare(long long C, int G, const double* sigt, const doubl
         X[e] = v;
         ext[e] = (T)ex;
         if (nsf) nsfT[e] = (T)nsf[e];
+        if (sigs1) {
+            y1[e] = (T)(1.5 * sigs1[e]);
+            cur[e] = T(0);
+        }
         if (G > 1)
             for (int gp = 0; gp < G; ++gp)
                 scat[((long long)gp * G + g) * C + c] = (T)(0.5 * sigs[((long long)gp * G + g) * C + c]);
@@ -687,6 +751,23 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
     T* phiprev = (T*)p;
     NOP_TRY(ctx->scratch("sn1d_psib", sizeof(T) * std::max<long long>(1, s.bnd_total), &p));
     T* psib = (T*)p;
+    // linearly anisotropic scattering (Eq. 25): fixed-source slabs, warp path
+    const bool p1 = ctx->sigs1_d != nullptr;
+    if (p1 && eigen) {
+        ctx->set_error("anisotropic scattering is supported for fixed-source problems");
+        return NOP_EINVAL;
+    }
+    T *y1 = nullptr, *cur = nullptr, *s1buf = nullptr, *jm = nullptr;
+    if (p1) {
+        NOP_TRY(ctx->scratch("sn1d_y1", sizeof(T) * G * C, &p));
+        y1 = (T*)p;
+        NOP_TRY(ctx->scratch("sn1d_cur", sizeof(T) * G * C, &p));
+        cur = (T*)p;
+        NOP_TRY(ctx->scratch("sn1d_s1", sizeof(T) * C, &p));
+        s1buf = (T*)p;
+        NOP_TRY(ctx->scratch("sn1d_jm", sizeof(T) * C, &p));
+        jm = (T*)p;
+    }
     NOP_TRY(ctx->scratch("sn1d_k0", sizeof(double) * B, &p));
     double* k0_d = (double*)p;
     NOP_TRY(ctx->scratch("sn1d_int", sizeof(int) * (5 * (size_t)B + 4), &p));
@@ -752,7 +833,7 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
     int smem_cells = 1;
     for (int b = 0; b < B; ++b) {
         const int h = s.order[b] / 2;
-        const bool fits = s.ncell[b] <= max_smem_cells;
+        const bool fits = s.ncell[b] <= max_smem_cells && !p1;
         const bool is_big =
             fits && (o->schedule == NOP_SCHED_BLOCK ||
                      (o->schedule == NOP_SCHED_AUTO && B > 1 && lat[b] > mean_load));
@@ -807,7 +888,8 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
     int mk = ctx->phase_begin(2);
     sn1d_prepare<T><<<std::max(1, pblocks), 256, 0, ctx->stream>>>(
         C, G, ctx->sigt_d, ctx->sigs_d, eigen ? nullptr : ctx->src_d,
-        eigen ? ctx->nsf_d : nullptr, phi0, (eigen && !phi0) ? 1 : 0, X, scat, ext, nsf);
+        eigen ? ctx->nsf_d : nullptr, phi0, (eigen && !phi0) ? 1 : 0, X, scat, ext, nsf,
+        p1 ? ctx->sigs1_d : nullptr, y1, cur);
     NOP_CUDA_TRY(ctx, cudaGetLastError());
     ctx->phase_end(mk);
     ctx->count_launch(false);
@@ -837,6 +919,11 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
     a.scat = scat;
     a.ext = ext;
     a.psib = psib;
+    a.p1 = p1 ? 1 : 0;
+    a.y1 = y1;
+    a.cur = cur;
+    a.s1buf = s1buf;
+    a.jm = jm;
     a.bc_left = ctx->bc[0];
     a.bc_right = ctx->bc[1];
     a.eigen = eigen ? 1 : 0;

@@ -19,7 +19,8 @@ def slab_batch_arrays(insts):
 def oracle_slab(s, bc=(0, 0)):
     P = T.uniform_slab(s.I, s.L, s.sigt, s.sigs, Q=s.Q, nusigf=s.nusigf,
                        bc_left=T.REFLECTIVE if bc[0] else T.VACUUM,
-                       bc_right=T.REFLECTIVE if bc[1] else T.VACUUM)
+                       bc_right=T.REFLECTIVE if bc[1] else T.VACUUM,
+                       sigs1=getattr(s, "sigs1", None))
     return P
 
 

@@ -225,3 +225,73 @@ def test_errors_and_caps(solver):
     assert info["rc"] == -4 and info["status"][0] == -4 and info["iterations"][0] == 3
     with pytest.raises(NopError):
         solver.solve_eigen(tol=1e-6)         # no production cross section
+
+
+# ------------------------------------------------- anisotropic scattering (Eq. 25)
+def _set_aniso(s, insts, bc=(0, 0)):
+    n, wdt, order, sigt, sigs, src, _ = slab_batch_arrays(insts)
+    s1 = np.concatenate([i.sigs1 if i.sigs1 is not None else np.zeros(i.I) for i in insts])
+    s.set_slabs(n, wdt, order, sigt, sigs, source=src, bc=bc, sigma_s1=s1)
+
+
+def _aniso_batch():
+    out = []
+    for b, (I, N, a1) in enumerate([(40, 4, 0.3), (75, 8, -0.2), (120, 16, 0.5), (33, 32, 0.0),
+                                    (64, 10, 0.25)]):
+        rng = np.random.default_rng(50 + b)
+        x = W.cell_centres(I)
+        st = 1.0 + 0.4 * np.sin(2 * np.pi * x / W.L_SLAB + b)
+        c = rng.uniform(0.5, 0.9, I)
+        out.append(W.Slab1G(I=I, N=N, sigt=st, sigs=c * st, Q=W.fourier_source(rng, x),
+                            sigs1=a1 * c * st))
+    return out
+
+
+@pytest.mark.parametrize("bc", [(0, 0), (1, 0), (0, 1)])
+def test_anisotropic_fp64_matches_oracle(solver, bc):
+    insts = _aniso_batch()
+    _set_aniso(solver, insts, bc=bc)
+    phi, info = solver.solve_fixed_source(tol=1e-12, itmax=100000, precision=1)
+    for s, g in zip(insts, split(phi, insts)):
+        r = T.source_iteration(oracle_slab(s, bc=bc), Qd.gauss_legendre(s.N), tol=1e-12,
+                               itmax=100000)
+        assert rel_l2(g, r.phi[0]) < 1e-9
+
+
+def test_anisotropic_case_fp32_within_tolerance(solver):
+    # Sec. 5.1 case with Sigma_s1 = 0.3: FP32 sweeps, same stopping rule
+    s = W.aniso_slab()
+    _set_aniso(solver, [s])
+    phi, info = solver.solve_fixed_source(tol=1e-6, itmax=100000, precision=0)
+    r = T.source_iteration(oracle_slab(s), Qd.gauss_legendre(s.N), tol=1e-6, itmax=100000)
+    assert abs(int(info["iterations"][0]) - r.iterations) <= 1
+    assert rel_l2(phi, r.phi[0]) < 1e-5
+    # the anisotropic term is not negligible in this case
+    iso = T.source_iteration(T.uniform_slab(s.I, s.L, s.sigt, s.sigs, Q=s.Q),
+                             Qd.gauss_legendre(s.N), tol=1e-10)
+    assert rel_l2(iso.phi[0], r.phi[0]) > 1e-3
+
+
+def test_anisotropic_warm_start_keeps_the_answer(solver):
+    # the recast warm start ignores Sigma_s1 (the operator knows isotropic
+    # scattering only); the model solve restores the anisotropic answer
+    from paper_2509_01416_gb300 import NOP_NO_DEEPONET, no_config
+    insts = [W.aniso_slab(seed=30 + b) for b in range(3)]
+    _set_aniso(solver, insts)
+    P = W.deeponet_init(4, m=128, width=64, p=32)
+    P["b3.W"] *= 2e-3
+    P["b3.b"] *= 2e-3
+    solver.no_set(no_config(NOP_NO_DEEPONET, sensors=128, width=64, basis=32), P)
+    plain, _ = solver.solve_fixed_source(tol=1e-10, itmax=100000, precision=1)
+    warm, wi = solver.solve_fixed_source(tol=1e-10, itmax=100000, precision=1, warm_start=1)
+    assert wi["recast_iterations"] > 0
+    assert rel_l2(warm, plain) < 1e-8
+
+
+def test_anisotropic_rejected_outside_fixed_source_slabs(solver):
+    from paper_2509_01416_gb300 import NopError
+    s = W.aniso_slab()
+    n, wdt, order, sigt, sigs, src, _ = slab_batch_arrays([s])
+    with pytest.raises(NopError):
+        solver.set_slabs(n, wdt, order, sigt, sigs, nu_sigma_f=0.5 * sigt, chi=[1.0],
+                         sigma_s1=s.sigs1)

@@ -65,6 +65,7 @@ class Slab1G:
     L: float = L_SLAB
     bc_left: int = 0          # 0 vacuum, 1 reflective
     bc_right: int = 0
+    sigs1: Optional[np.ndarray] = None   # first Legendre moment (Eq. 25), or None
 
 
 # ---------------------------------------------------------------------------
@@ -181,6 +182,17 @@ def config4(seed=4, n=256, L=10.0):
         nsf[:, msk] = nf[:, None]
     return XYMG(nx=n, ny=n, Lx=L, Ly=L, sigt=sigt, sigs=sigs, nusigf=nsf, chi=chi,
                 bc={"x0": 1, "xL": 0, "y0": 1, "yL": 0})
+
+
+def aniso_slab(seed=25, I=100, N=32, sigt=1.2, sigs0=0.8, sigs1=0.3):
+    """The fixed-source slab with linearly anisotropic scattering of Sec. 5.1
+    Eq. 25 (Sigma_t 1.2, Sigma_s0 0.8, Sigma_s1 0.3, 10 cm, dL = 0.1 cm, S32),
+    with a GRF source of unit integral drawn from the seed."""
+    rng = np.random.default_rng(seed)
+    x = cell_centres(I)
+    one = np.ones(I)
+    return Slab1G(I=I, N=N, sigt=sigt * one, sigs=sigs0 * one, Q=grf(rng, x, 1)[0],
+                  sigs1=sigs1 * one)
 
 
 def slab_instance(rng, I, N):
