@@ -166,7 +166,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--train-steps", type=int, default=3000,
+    ap.add_argument("--train-steps", type=int, default=10000,
                     help="Adam steps of the operator's training (0: untrained operator, "
                          "no training set; for profiling runs)")
     ap.add_argument("--instances", type=int, default=0,
