@@ -358,167 +358,7 @@ __global__ void trunk_dot_kernel(long long c0, int n, int p, const float* Tn, co
 // layer 1 (elementwise, K = 1), layers 2-4 on mma.sync (BF16 operands, FP32
 // accumulation, activations rounded to BF16 between layers like the generic
 // GEMM), then the inner product with its instance's coefficients.
-constexpr int FT_W = 128, FT_PAD = 8, FT_WARPS = 8, FT_MT = 2, FT_PTS = 16 * FT_MT * FT_WARPS;
-
-__device__ __forceinline__ void ft_mma(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
-                                       uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-        "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// The trunk depends on the cell centre x = (i + 0.5) / I only, so instances
-// with the same cell count I share it: the kernel walks the distinct points
-// (groups of instances with equal I, CSR lists) and writes the inner product
-// with every instance of the group.  Every warp owns 32 points (two m16
-// tiles), so each weight fragment loaded from shared memory feeds two
-// tensor-core instructions.
-__global__ void __launch_bounds__(32 * FT_WARPS) trunk_fused_kernel(
-    long long P, int NG, const long long* grp_pt_off, const int* grp_I, const int* grp_inst_off,
-    const int* inst_list, const long long* cell_off, const float* W1, const float* b1,
-    const float* W2, const float* b2, const float* W3, const float* b3, const float* W4,
-    const float* b4, const float* beta_keep, const int* status, double* phi) {
-    extern __shared__ __align__(16) unsigned char ft_smem[];
-    __nv_bfloat16(*Ws)[FT_W][FT_W + FT_PAD] = (__nv_bfloat16(*)[FT_W][FT_W + FT_PAD])ft_smem;
-    __nv_bfloat16(*H)[FT_W + FT_PAD] =
-        (__nv_bfloat16(*)[FT_W + FT_PAD])(ft_smem + 3 * sizeof(__nv_bfloat16) * FT_W * (FT_W + FT_PAD));
-    __shared__ float bs[4][FT_W], w1s[FT_W];
-    __shared__ int pgrp[FT_PTS], pidx[FT_PTS];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int gq = lane >> 2, tq = lane & 3;
-    for (int e = tid; e < FT_W * FT_W; e += blockDim.x) {
-        const int n = e / FT_W, k = e % FT_W;
-        Ws[0][n][k] = __float2bfloat16_rn(W2[e]);
-        Ws[1][n][k] = __float2bfloat16_rn(W3[e]);
-        Ws[2][n][k] = __float2bfloat16_rn(W4[e]);
-    }
-    for (int n = tid; n < FT_W; n += blockDim.x) {
-        // the trunk input weights are rounded to BF16 like any GEMM operand
-        w1s[n] = __bfloat162float(__float2bfloat16_rn(W1[n]));
-        bs[0][n] = b1[n];
-        bs[1][n] = b2[n];
-        bs[2][n] = b3[n];
-        bs[3][n] = b4[n];
-    }
-    __syncthreads();
-    const int r0 = warp * 16 * FT_MT;
-    for (long long t0 = (long long)blockIdx.x * FT_PTS; t0 < P; t0 += (long long)gridDim.x * FT_PTS) {
-        // group and coordinate of the warp's 32 points, one lane each
-        float xl = 0.f;
-        {
-            const long long c = t0 + r0 + lane;
-            int g = -1, i = 0;
-            if (c < P) {
-                int lo = 0, hi = NG - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (grp_pt_off[mid] <= c) lo = mid;
-                    else hi = mid - 1;
-                }
-                g = lo;
-                i = (int)(c - grp_pt_off[lo]);
-                xl = (float)((i + 0.5) / grp_I[lo]);
-            }
-            pgrp[r0 + lane] = g;
-            pidx[r0 + lane] = i;
-        }
-        // layer 1 for the warp's points: h = relu(x w1 + b1), BF16
-        for (int rr = 0; rr < 16 * FT_MT; ++rr) {
-            const float x = __shfl_sync(0xffffffffu, xl, rr);
-            const float xb = __bfloat162float(__float2bfloat16_rn(x));
-            for (int n = lane; n < FT_W; n += 32)
-                H[r0 + rr][n] = __float2bfloat16_rn(fmaxf(xb * w1s[n] + bs[0][n], 0.f));
-        }
-        __syncwarp();
-        float acc[FT_MT][16][4];
-        for (int l = 0; l < 3; ++l) {
-#pragma unroll
-            for (int mt = 0; mt < FT_MT; ++mt)
-#pragma unroll
-                for (int nt = 0; nt < 16; ++nt)
-#pragma unroll
-                    for (int c4 = 0; c4 < 4; ++c4) acc[mt][nt][c4] = 0.f;
-#pragma unroll 2
-            for (int kk = 0; kk < FT_W; kk += 16) {
-                uint32_t af[FT_MT][4];
-#pragma unroll
-                for (int mt = 0; mt < FT_MT; ++mt) {
-                    const int r = r0 + mt * 16 + gq;
-                    af[mt][0] = *(const uint32_t*)&H[r][kk + 2 * tq];
-                    af[mt][1] = *(const uint32_t*)&H[r + 8][kk + 2 * tq];
-                    af[mt][2] = *(const uint32_t*)&H[r][kk + 2 * tq + 8];
-                    af[mt][3] = *(const uint32_t*)&H[r + 8][kk + 2 * tq + 8];
-                }
-#pragma unroll
-                for (int nt = 0; nt < 16; ++nt) {
-                    const int n = nt * 8 + gq;
-                    const uint32_t b0 = *(const uint32_t*)&Ws[l][n][kk + 2 * tq];
-                    const uint32_t b1v = *(const uint32_t*)&Ws[l][n][kk + 2 * tq + 8];
-#pragma unroll
-                    for (int mt = 0; mt < FT_MT; ++mt) ft_mma(acc[mt][nt], af[mt], b0, b1v);
-                }
-            }
-            __syncwarp();
-            if (l < 2) {
-#pragma unroll
-                for (int mt = 0; mt < FT_MT; ++mt)
-#pragma unroll
-                    for (int nt = 0; nt < 16; ++nt)
-#pragma unroll
-                        for (int h2 = 0; h2 < 2; ++h2)
-#pragma unroll
-                            for (int cc = 0; cc < 2; ++cc) {
-                                const int n = nt * 8 + 2 * tq + cc;
-                                H[r0 + mt * 16 + gq + 8 * h2][n] = __float2bfloat16_rn(
-                                    fmaxf(acc[mt][nt][2 * h2 + cc] + bs[l + 1][n], 0.f));
-                            }
-                __syncwarp();
-            }
-        }
-        // output layer values + bias (BF16 operands), then the inner product
-        // with the coefficients of every instance of the point's group
-#pragma unroll
-        for (int mt = 0; mt < FT_MT; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < 16; ++nt)
-#pragma unroll
-                for (int h2 = 0; h2 < 2; ++h2)
-#pragma unroll
-                    for (int cc = 0; cc < 2; ++cc)
-                        acc[mt][nt][2 * h2 + cc] = __bfloat162float(__float2bfloat16_rn(
-                            acc[mt][nt][2 * h2 + cc] + bs[3][nt * 8 + 2 * tq + cc]));
-#pragma unroll
-        for (int mt = 0; mt < FT_MT; ++mt)
-#pragma unroll
-            for (int h2 = 0; h2 < 2; ++h2) {
-                const int row = r0 + mt * 16 + gq + 8 * h2;
-                const int g = pgrp[row], i = pidx[row];
-                const int k0 = g >= 0 ? grp_inst_off[g] : 0;
-                const int nk = g >= 0 ? grp_inst_off[g + 1] - k0 : 0;
-                int kmax = nk;   // warp-uniform trip count for the shuffles
-                for (int o = 16; o > 0; o >>= 1) kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
-                for (int k = 0; k < kmax; ++k) {
-                    const int b = k < nk ? inst_list[k0 + k] : -1;
-                    float d = 0.f;
-                    if (b >= 0 && (!status || status[b] != 3)) {
-                        const float* be = beta_keep + (long long)b * FT_W;
-#pragma unroll
-                        for (int nt = 0; nt < 16; ++nt)
-#pragma unroll
-                            for (int cc = 0; cc < 2; ++cc)
-                                d += acc[mt][nt][2 * h2 + cc] *
-                                     __bfloat162float(__float2bfloat16_rn(be[nt * 8 + 2 * tq + cc]));
-                    }
-                    d += __shfl_xor_sync(0xffffffffu, d, 1);
-                    d += __shfl_xor_sync(0xffffffffu, d, 2);
-                    if (tq == 0 && b >= 0) phi[cell_off[b] + i] = d;
-                }
-            }
-        __syncwarp();
-    }
-}
+constexpr int FT_W = 128;
 
 __global__ void bin_centres_kernel(int M, float* X) {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -738,11 +578,6 @@ int deeponet_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* sta
     // final flux at every cell centre
     const long long C = s.C;
     if (c.width == FT_W && c.basis == FT_W && c.depth == 4) {
-        const size_t smem = 3 * sizeof(__nv_bfloat16) * FT_W * (FT_W + FT_PAD) +
-                            sizeof(__nv_bfloat16) * FT_PTS * (FT_W + FT_PAD);
-        NOP_CUDA_TRY(ctx, cudaFuncSetAttribute(trunk_fused_kernel,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem));
         // instances grouped by cell count (CSR): distinct points once
         std::vector<int> order(B);
         std::iota(order.begin(), order.end(), 0);
@@ -774,15 +609,39 @@ int deeponet_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* sta
                                           cudaMemcpyHostToDevice, ctx->stream));
         NOP_CUDA_TRY(ctx, cudaMemcpyAsync(gI_d, ints.data(), sizeof(int) * ints.size(),
                                           cudaMemcpyHostToDevice, ctx->stream));
-        const int grid = (int)std::max<long long>(
-            1, std::min<long long>((P + FT_PTS - 1) / FT_PTS, ctx->sm_count));
-        trunk_fused_kernel<<<grid, 32 * FT_WARPS, smem, ctx->stream>>>(
-            P, NG, gpt_d, gI_d, ginst_d, list_d, s.cell_off_d, Wp(ctx, 1, 0), Bp(ctx, 1, 0),
-            Wp(ctx, 1, 1), Bp(ctx, 1, 1), Wp(ctx, 1, 2), Bp(ctx, 1, 2), Wp(ctx, 1, 3),
-            Bp(ctx, 1, 3), beta_keep, status, phi_d);
-        NOP_CUDA_TRY(ctx, cudaGetLastError());
-        ctx->count_launch(false);
+        // per 128-point tile: first and last group, instance range
+        const long long ntile = (P + 127) / 128;
+        std::vector<int4> tinfo((size_t)ntile);
+        {
+            int gg = 0;
+            for (long long tt = 0; tt < ntile; ++tt) {
+                const long long p0 = tt * 128, p1 = std::min(P, p0 + 128) - 1;
+                while (gpt[gg + 1] <= p0) ++gg;
+                int gl = gg;
+                while (gpt[gl + 1] <= p1) ++gl;
+                tinfo[(size_t)tt] = make_int4(gg, gl, ginst[gg], ginst[gl + 1]);
+            }
+        }
+        NOP_TRY(ctx->scratch("ft_tinfo", sizeof(int4) * (size_t)ntile, &q));
+        int4* tinfo_d = (int4*)q;
+        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(tinfo_d, tinfo.data(), sizeof(int4) * (size_t)ntile,
+                                          cudaMemcpyHostToDevice, ctx->stream));
+        NOP_TRY(ctx->scratch("tc_err", sizeof(int), &q));
+        int* err_d = (int*)q;
+        NOP_CUDA_TRY(ctx, cudaMemsetAsync(err_d, 0, sizeof(int), ctx->stream));
+        const float* const TW[4] = {Wp(ctx, 1, 0), Wp(ctx, 1, 1), Wp(ctx, 1, 2), Wp(ctx, 1, 3)};
+        const float* const TB[4] = {Bp(ctx, 1, 0), Bp(ctx, 1, 1), Bp(ctx, 1, 2), Bp(ctx, 1, 3)};
+        NOP_TRY(trunk_tc_launch(ctx, P, tinfo_d, gpt_d, gI_d, ginst_d, list_d, s.cell_off_d, TW,
+                                TB, beta_keep, status, phi_d, err_d));
         ctx->phase_end(mk);
+        int herr = 0;
+        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(&herr, err_d, sizeof(int), cudaMemcpyDeviceToHost,
+                                          ctx->stream));
+        NOP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+        if (herr) {
+            ctx->set_error("trunk evaluation: tensor-core completion wait timed out");
+            return NOP_ETIMEOUT;
+        }
         if (status_d)
             NOP_CUDA_TRY(ctx, cudaMemcpyAsync(status_d, status, sizeof(int) * B,
                                               cudaMemcpyDeviceToDevice, ctx->stream));

@@ -185,6 +185,16 @@ int recast_fused_run(nop_ctx* ctx, int B, double h, double tol, int itmax, const
                      const float* Tref, float* beta, float* beta_keep, int* status, int* iters,
                      double* prev, int* run, int* active2, int* its);
 
+// Final DeepONet flux of the 128-wide depth-4 trunk on tcgen05 tensor cores
+// (trunk_tc.cu): distinct points in CSR groups of instances with equal cell
+// counts; err (device int) is set if a completion wait timed out.
+// tinfo: per 128-point tile {first group, last group, first and end index
+// into the instance list}.
+int trunk_tc_launch(nop_ctx* ctx, long long P, const int4* tinfo, const long long* gpt,
+                    const int* gI, const int* ginst, const int* list, const long long* cell_off,
+                    const float* const W[4], const float* const b[4], const float* beta_keep,
+                    const int* status, double* phi, int* err);
+
 // 2D x-y solver (sn2d.cu)
 int xy_solve(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* phi0, double k0,
              double* phi_out, bool out_dev, double* k_out, nop_stats* st);
