@@ -200,5 +200,5 @@ int xy_solve(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
              double* phi_out, bool out_dev, double* k_out, nop_stats* st);
 
 // Lane split of the 1D sweep (log2 lanes per angle group, angles per lane).
-void sn1d_pick_config(int cells, int order, int* lg_ng, int* A);
+void sn1d_pick_config(int cells, int order, int* lg_ng, int* A, bool pow2 = false);
 }  // namespace nop

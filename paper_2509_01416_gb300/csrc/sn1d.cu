@@ -22,16 +22,21 @@ extern template int sn1d_run<double>(nop_ctx*, const nop_solve_opts*, bool, cons
 // Chunked splits add the map-composition pass and a scan.  A lane carries
 // A in {1, 2, 4} angles (the compiled variants; wider lanes would raise the
 // kernel's register count and cut its occupancy).
-void sn1d_pick_config(int I, int N, int* lg_out, int* A_out) {
+void sn1d_pick_config(int I, int N, int* lg_out, int* A_out, bool pow2) {
+    // A angles per lane: any count up to 6 (powers of two only when asked),
+    // so that ng x A covers the half-angle set with few idle slots
     const int h = N / 2;
     double best = 1e300;
     int bl = 5, bA = 4;
     for (int lg = 0; lg <= 5; ++lg) {
         const int ng = 1 << lg, nt = 32 >> lg;
         const int need = (h + ng - 1) / ng;
-        int A = 1;
-        while (A < need) A <<= 1;
-        if (A > 4) continue;
+        int A = need;
+        if (pow2) {
+            A = 1;
+            while (A < need) A <<= 1;
+        }
+        if (A > (pow2 ? 4 : 6)) continue;
         const double m = (double)((I + nt - 1) / nt);
         const double mufu = 8.0 * A;
         const double passB = std::max(mufu, 12.0 + 2.0 * lg + 13.0 * A);

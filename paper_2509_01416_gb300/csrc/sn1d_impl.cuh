@@ -606,6 +606,7 @@ __device__ __forceinline__ void dispatch(const Sn1dArgs& a, const Grp& gr, const
                                          int inst) {
     const int cfg = a.cfg[inst];
     const int A = cfg & 0xff, lg = cfg >> 8;
+    // anisotropic instances take A in {1, 2, 4} only (the host picks so)
     switch (A) {
         case 1:
             if (a.p1 && !gr.block) solve_instance<T, 1, true>(a, gr, sg, inst, lg);
@@ -614,6 +615,17 @@ __device__ __forceinline__ void dispatch(const Sn1dArgs& a, const Grp& gr, const
         case 2:
             if (a.p1 && !gr.block) solve_instance<T, 2, true>(a, gr, sg, inst, lg);
             else solve_instance<T, 2, false>(a, gr, sg, inst, lg);
+            break;
+        // 3, 5 and 6 angles per lane in FP32 only (the FP64 path picks powers
+        // of two and keeps the kernel small)
+        case 3:
+            if constexpr (sizeof(T) == 4) solve_instance<T, 3, false>(a, gr, sg, inst, lg);
+            break;
+        case 5:
+            if constexpr (sizeof(T) == 4) solve_instance<T, 5, false>(a, gr, sg, inst, lg);
+            break;
+        case 6:
+            if constexpr (sizeof(T) == 4) solve_instance<T, 6, false>(a, gr, sg, inst, lg);
             break;
         default:
             if (a.p1 && !gr.block) solve_instance<T, 4, true>(a, gr, sg, inst, lg);
@@ -821,7 +833,7 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
     double lat_sum = 0, big_work = 0, small_work = 0;
     for (int b = 0; b < B; ++b) {
         int lg, A;
-        sn1d_pick_config(s.ncell[b], s.order[b], &lg, &A);
+        sn1d_pick_config(s.ncell[b], s.order[b], &lg, &A, p1 || sizeof(T) == 8);
         cfg[b] = (lg << 8) | A;
         const int nt = 32 >> lg;
         const double steps = (nt > 1 ? 4.0 : 2.0) * ((s.ncell[b] + nt - 1) / nt) * G;
@@ -840,7 +852,7 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
         if (is_big) {
             int lg, A;
             const int hw = (h + SN1D_THREADS / 32 - 1) / (SN1D_THREADS / 32);
-            sn1d_pick_config(s.ncell[b], 2 * hw, &lg, &A);
+            sn1d_pick_config(s.ncell[b], 2 * hw, &lg, &A, sizeof(T) == 8);
             cfg[b] = (lg << 8) | A;
             big.push_back(b);
             smem_cells = std::max(smem_cells, s.ncell[b]);
