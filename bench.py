@@ -169,6 +169,8 @@ def main():
     ap.add_argument("--train-steps", type=int, default=10000,
                     help="Adam steps of the operator's training (0: untrained operator, "
                          "no training set; for profiling runs)")
+    ap.add_argument("--recast-tol", type=float, default=RECAST_TOL)
+    ap.add_argument("--recast-itmax", type=int, default=RECAST_ITMAX)
     ap.add_argument("--instances", type=int, default=0,
                     help="solve only the first N instances of the batch (profiling aid)")
     args = ap.parse_args()
@@ -226,7 +228,8 @@ def main():
     def step(warm=True):
         return s.solve_fixed_source_dev(phi_dev.data_ptr(), tol=TOL, itmax=200000,
                                         precision=0, warm_start=1 if warm else 0,
-                                        recast_tol=RECAST_TOL, recast_itmax=RECAST_ITMAX)
+                                        recast_tol=args.recast_tol,
+                                        recast_itmax=args.recast_itmax)
 
     def barrier():
         if world > 1:
@@ -284,7 +287,8 @@ def main():
     for _ in range(args.steps):
         s.set_slabs(hn, hw, ho, hst, hss, source=hsrc)
         s.solve_fixed_source(tol=TOL, itmax=200000, precision=0, warm_start=1,
-                             recast_tol=RECAST_TOL, recast_itmax=RECAST_ITMAX, out=phi_h)
+                             recast_tol=args.recast_tol, recast_itmax=args.recast_itmax,
+                             out=phi_h)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_value = whole_job_rate(world, B, args.steps, max_over_ranks(e2e_s, world, "cuda"))
@@ -333,7 +337,7 @@ def main():
                    "l2": "inputs larger than L2: %.0f MB resident per GPU" %
                          ((Ctot * (3 * 8 + 24)) / 1e6),
                    "warm_start": "DeepONet (128 sensors, 4x128, p=128, BF16) recast, "
-                                 "tol %g, itmax %d" % (RECAST_TOL, RECAST_ITMAX)},
+                                 "tol %g, itmax %d" % (args.recast_tol, args.recast_itmax)},
         "plain_guess": {"value": plain_value, "unit": UNIT,
                         "ms_per_step": plain_ms / max(1, args.steps // 2),
                         "iterations_mean": float(np.mean(plain_iters)),
