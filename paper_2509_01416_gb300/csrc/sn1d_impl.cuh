@@ -271,7 +271,7 @@ __device__ __forceinline__ void sweep_half(const bool block, Cell4<T>* X, Cell2<
             psi[q].set((psi_bnd[q] + Be) - De * psi_bnd[q]);
         }
     }
-#pragma unroll 2
+#pragma unroll 1
     for (int k = 0; k < m; ++k) {
         const bool valid = k < len;
         const int i = MINUS ? (I - 1 - (k0 + k)) : (k0 + k);
