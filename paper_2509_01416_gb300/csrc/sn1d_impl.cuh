@@ -219,6 +219,7 @@ __device__ __forceinline__ void sweep_half(const bool block, Cell4<T>* X, Cell2<
             Bc[q].set(T(0));
             D[q] = T(0);
         }
+#pragma unroll 1
         for (int k = 0; k < len; ++k) {
             const int i = MINUS ? (I - 1 - (k0 + k)) : (k0 + k);
             T st, s;
