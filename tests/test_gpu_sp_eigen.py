@@ -233,3 +233,38 @@ def test_cp_two_group_2d_matches_oracle(solver):
                                    tol_phi=1e-30, itmax=2)
     assert abs(k[0] - kr) < 1e-2 * abs(kr), (k[0], kr)
     assert rel_l2(phi, pr.reshape(-1)) < 2e-2
+
+
+def test_config4_full_size_fno2d_warm_start(solver):
+    """The 256 x 256, 8-group x-y eigenproblem with the FNO-2D of the
+    workload (width 32, 16 x 16 modes, 4 layers) trained at p* on a few
+    solver-generated p* solutions of the same geometry: the simple-
+    preconditioning warm start (or its fallback) must leave the eigenpair of
+    the model solve unchanged at full size."""
+    from paper_2509_01416_gb300 import NOP_NO_FNO2D, no_config
+    from paper_2509_01416_gb300 import train as TR
+    c = W.config4()
+    bc = tuple(c.bc[f] for f in ("x0", "xL", "y0", "yL"))
+    cfg = no_config(NOP_NO_FNO2D, width=32, modes=16, depth=4, proj=128, length=c.Lx)
+    solver.no_set(cfg, W.fno2d_init(4, width=32, modes=16, proj=128))
+    import time
+    t0 = time.perf_counter()
+    S, Y = TR.fno2d_training_set(solver, cfg, W.training_sources_2d(6, 8, c.nx), bc=bc)
+    t1 = time.perf_counter()
+    hist = TR.train_fno(solver, S, Y, steps=40, batch=2, seed=2, lr=2e-3)
+    t2 = time.perf_counter()
+    assert np.all(np.isfinite(hist)) and hist[-10:].mean() < hist[:10].mean()
+    solver.set_xy(c.nx, c.ny, c.Lx, c.Ly, c.sigt.reshape(-1), c.sigs.reshape(-1),
+                  nu_sigma_f=c.nusigf.reshape(-1), chi=c.chi, bc=bc)
+    kw = dict(tol=1e-6, tol_k=1e-7, tol_inner=1e-6, itmax=2000, itmax_inner=500, check=False)
+    kp, php, ip = solver.solve_eigen(**kw)
+    t3 = time.perf_counter()
+    kw_, phw, iw = solver.solve_eigen(warm_start=1, recast_tol=1e-2, recast_itmax=10, **kw)
+    t4 = time.perf_counter()
+    print("\nconfig4 FNO-2D: data %.1f s, training %.1f s, plain solve %.1f s (outer %d), "
+          "warm solve %.1f s (outer %d, recast %d, status %d)" % (
+              t1 - t0, t2 - t1, t3 - t2, ip["outer"], t4 - t3, iw["outer"],
+              iw["recast_iterations"], iw["recast_status"]))
+    assert iw["recast_iterations"] > 0
+    assert abs(kw_[0] - kp[0]) < 1e-6, (kw_, kp, iw)
+    assert rel_l2(phw, php) < 1e-4

@@ -236,7 +236,7 @@ def training_sources_2d(seed, n_samples, n, L=10.0, ell=1.2, var=3e-4, mean=0.07
     C = np.exp(-d * d / (2 * ell * ell)) + 1e-10 * np.eye(n)
     Lc = np.linalg.cholesky(C)
     z = rng.standard_normal((n_samples, n, n))
-    f = np.sqrt(var) * np.einsum("ij,bjk,lk->bil", Lc, z, Lc)
+    f = np.sqrt(var) * np.matmul(np.matmul(Lc, z), Lc.T)   # Lc z Lc^T per sample
     s = np.maximum(mean + f, 0.0)
     h = L / n
     return s / (s.sum(axis=(1, 2), keepdims=True) * h * h)
