@@ -211,7 +211,9 @@ class Solver:
         n_cells = np.ascontiguousarray(n_cells, dtype=np.int32)
         order = np.ascontiguousarray(order, dtype=np.int32)
         width = capi._f64(width)
-        G = int(np.asarray(sigma_t).size // int(n_cells.sum()))
+        total = int(n_cells.sum())
+        # an empty batch reaches the library, which rejects it
+        G = int(np.asarray(sigma_t).size // total) if total > 0 else 1
         arrs = [capi._f64(sigma_t), capi._f64(sigma_s),
                 None if source is None else capi._f64(source),
                 None if nu_sigma_f is None else capi._f64(nu_sigma_f),
