@@ -46,7 +46,7 @@ WORKLOAD = ("4096 slabs, cells U{64..2048}, GL S_N N even U{8..64}, sinusoidal o
 def rank_instances(rank, limit=0):
     """The rank's own batch: the 4096-slab recipe seeded by the rank (weak
     scaling; ranks share no instances and exchange no data)."""
-    return W.config5(seed=5 + rank, n_inst=limit if limit > 0 else 4096)
+    return W.slab_batch(seed=5 + rank, n_inst=limit if limit > 0 else 4096)
 
 
 def max_over_ranks(x, world, device):

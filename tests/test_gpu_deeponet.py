@@ -164,7 +164,7 @@ def test_trained_operator_cuts_iterations(solver):
     U, X, Y, _ = TR.deeponet_training_set(solver, cfg, src, order=32)
     hist = TR.train(solver, U, X, Y, steps=1500, batch=100, seed=2)
     assert hist[-50:].mean() < 0.2 * hist[:50].mean()
-    c = W.config2()
+    c = W.hetero_slab_s32()
     n, wdt, order, sigt, sigs, s2, _ = slab_batch_arrays([c])
     solver.set_slabs(n, wdt, order, sigt, sigs, source=s2)
     plain, pi = solver.solve_fixed_source(tol=1e-6, precision=0)

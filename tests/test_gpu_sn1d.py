@@ -45,8 +45,8 @@ def test_gauss_legendre_on_device_matches_oracle(solver):
         assert np.max(np.abs(mu - m0)) < 1e-14 and np.max(np.abs(w - w0)) < 1e-14
 
 
-def test_config1_fp64_matches_oracle_iteration_for_iteration(solver):
-    c = W.config1()
+def test_uniform_slab_fp64_matches_oracle_iteration_for_iteration(solver):
+    c = W.uniform_slab_s16()
     _set(solver, [c])
     phi, info = solver.solve_fixed_source(tol=1e-8, itmax=10000, precision=1)
     r = T.source_iteration(oracle_slab(c), Qd.gauss_legendre(c.N), tol=1e-8)
@@ -55,8 +55,8 @@ def test_config1_fp64_matches_oracle_iteration_for_iteration(solver):
     assert info["status"][0] == 0
 
 
-def test_config2_fp32_within_workload_tolerance(solver):
-    c = W.config2()
+def test_heterogeneous_slab_fp32_within_workload_tolerance(solver):
+    c = W.hetero_slab_s32()
     _set(solver, [c])
     quad = Qd.gauss_legendre(c.N)
     phi, info = solver.solve_fixed_source(tol=1e-6, itmax=20000, precision=0)
@@ -68,8 +68,8 @@ def test_config2_fp32_within_workload_tolerance(solver):
     assert rel_l2(tight, conv.phi[0]) <= 1e-5, info2
 
 
-def test_config3_eigen_fp32(solver):
-    c = W.config3()
+def test_three_region_eigen_fp32(solver):
+    c = W.eigen_slab_s32()
     _set(solver, [c])
     quad = Qd.gauss_legendre(c.N)
     # same stopping rule on both sides (tol 1e-6 flux, 1e-7 in k, inner 1e-6)
@@ -171,8 +171,8 @@ def test_ragged_batch_fp32_same_rule(solver):
         assert rel_l2(ph, r.phi[0]) <= 1e-5, (s.I, s.N)
 
 
-def test_full_batch_config5_sampled(solver):
-    insts = W.config5()
+def test_full_4096_slab_batch_sampled(solver):
+    insts = W.slab_batch()
     _set(solver, insts)
     phi, info = solver.solve_fixed_source(tol=1e-6, itmax=50000, precision=0)
     assert np.all(info["status"] == 0)
@@ -219,7 +219,7 @@ def test_errors_and_caps(solver):
         solver.set_slabs([5], [1.0], [3], np.ones(5), np.zeros(5), source=np.ones(5))
     with pytest.raises(NopError):
         solver.set_slabs([5], [1.0], [4], -np.ones(5), np.zeros(5), source=np.ones(5))
-    c = W.config1()
+    c = W.uniform_slab_s16()
     _set(solver, [c])
     phi, info = solver.solve_fixed_source(tol=1e-12, itmax=3, precision=0, check=False)
     assert info["rc"] == -4 and info["status"][0] == -4 and info["iterations"][0] == 3

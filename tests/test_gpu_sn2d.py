@@ -95,7 +95,7 @@ def test_infinite_medium_fp32(solver):
 
 
 def test_eigen_fp64_matches_oracle_same_rule(solver):
-    c = W.config4(seed=7, n=16)
+    c = W.checkerboard_xy_8g(seed=7, n=16)
     bc = tuple(c.bc[f] for f in FACES)
     _set(solver, c.nx, c.ny, c.Lx, c.Ly, c.sigt, c.sigs, nsf=c.nusigf, chi=c.chi, bc=bc)
     k, phi, info = solver.solve_eigen(tol=1e-8, tol_k=1e-10, tol_inner=1e-9, itmax=2000,
@@ -107,9 +107,9 @@ def test_eigen_fp64_matches_oracle_same_rule(solver):
     assert rel_l2(phi, e.phi.reshape(-1)) < 1e-8
 
 
-def test_config4_recipe_fp32_reduced_mesh(solver):
+def test_checkerboard_recipe_fp32_reduced_mesh(solver):
     # the 8-group checkerboard recipe at 48 x 48: FP32 sweeps vs converged oracle
-    c = W.config4(n=48)
+    c = W.checkerboard_xy_8g(n=48)
     bc = tuple(c.bc[f] for f in FACES)
     _set(solver, c.nx, c.ny, c.Lx, c.Ly, c.sigt, c.sigs, nsf=c.nusigf, chi=c.chi, bc=bc)
     k, phi, info = solver.solve_eigen(tol=1e-7, tol_k=1e-9, tol_inner=1e-7, itmax=2000,
@@ -121,8 +121,8 @@ def test_config4_recipe_fp32_reduced_mesh(solver):
     assert rel_l2(phi, e.phi.reshape(-1)) <= 1e-5
 
 
-def test_config4_full_size_properties(solver):
-    c = W.config4()
+def test_checkerboard_full_size_properties(solver):
+    c = W.checkerboard_xy_8g()
     bc = tuple(c.bc[f] for f in FACES)
     _set(solver, c.nx, c.ny, c.Lx, c.Ly, c.sigt, c.sigs, nsf=c.nusigf, chi=c.chi, bc=bc)
     k, phi, info = solver.solve_eigen(tol=1e-6, tol_k=1e-7, tol_inner=1e-6, itmax=2000,

@@ -235,7 +235,7 @@ def test_cp_two_group_2d_matches_oracle(solver):
     assert rel_l2(phi, pr.reshape(-1)) < 2e-2
 
 
-def test_config4_full_size_fno2d_warm_start(solver):
+def test_checkerboard_full_size_fno2d_warm_start(solver):
     """The 256 x 256, 8-group x-y eigenproblem with the FNO-2D of the
     workload (width 32, 16 x 16 modes, 4 layers) trained at p* on a few
     solver-generated p* solutions of the same geometry: the simple-
@@ -243,7 +243,7 @@ def test_config4_full_size_fno2d_warm_start(solver):
     the model solve unchanged at full size."""
     from paper_2509_01416_gb300 import NOP_NO_FNO2D, no_config
     from paper_2509_01416_gb300 import train as TR
-    c = W.config4()
+    c = W.checkerboard_xy_8g()
     bc = tuple(c.bc[f] for f in ("x0", "xL", "y0", "yL"))
     cfg = no_config(NOP_NO_FNO2D, width=32, modes=16, depth=4, proj=128, length=c.Lx)
     solver.no_set(cfg, W.fno2d_init(4, width=32, modes=16, proj=128))
@@ -261,7 +261,7 @@ def test_config4_full_size_fno2d_warm_start(solver):
     t3 = time.perf_counter()
     kw_, phw, iw = solver.solve_eigen(warm_start=1, recast_tol=1e-2, recast_itmax=10, **kw)
     t4 = time.perf_counter()
-    print("\nconfig4 FNO-2D: data %.1f s, training %.1f s, plain solve %.1f s (outer %d), "
+    print("\ncheckerboard FNO-2D: data %.1f s, training %.1f s, plain solve %.1f s (outer %d), "
           "warm solve %.1f s (outer %d, recast %d, status %d)" % (
               t1 - t0, t2 - t1, t3 - t2, ip["outer"], t4 - t3, iw["outer"],
               iw["recast_iterations"], iw["recast_status"]))

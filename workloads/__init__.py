@@ -69,15 +69,15 @@ class Slab1G:
 
 
 # ---------------------------------------------------------------------------
-# the five workloads
+# the workloads
 # ---------------------------------------------------------------------------
-def config1():
+def uniform_slab_s16():
     """200 cells, width 10, Sigma_t 1.0, Sigma_s 0.9, Q = 1, vacuum, S16."""
     I = 200
     return Slab1G(I=I, N=16, sigt=np.full(I, 1.0), sigs=np.full(I, 0.9), Q=np.ones(I))
 
 
-def config2(seed=2):
+def hetero_slab_s32(seed=2):
     """512 cells, S32, sinusoidal Sigma_t, piecewise scattering ratio, Fourier Q."""
     rng = np.random.default_rng(seed)
     I = 512
@@ -99,7 +99,7 @@ def _bare_slab_nonleakage(sigt, sigs, L):
     return sa / (sa + D * B * B)
 
 
-def config3(seed=3):
+def eigen_slab_s32(seed=3):
     """1000 cells, S32, 3 regions, Sigma_t in [0.8, 1.5], c in [0.6, 0.9],
     production scaled so that k lands near [0.9, 1.1], vacuum."""
     rng = np.random.default_rng(seed)
@@ -156,7 +156,7 @@ def base_table_8g():
     return sigt, S, nsf * (KINF_8G / kinf), chi
 
 
-def config4(seed=4, n=256, L=10.0):
+def checkerboard_xy_8g(seed=4, n=256, L=10.0):
     """256x256, 8 groups, 4x4 checkerboard of 16 material sets drawn +-30%
     around the base table; reflective x=0 and y=0, vacuum x=L and y=L."""
     rng = np.random.default_rng(seed)
@@ -196,7 +196,7 @@ def aniso_slab(seed=25, I=100, N=32, sigt=1.2, sigs0=0.8, sigs1=0.3):
 
 
 def slab_instance(rng, I, N):
-    """One config-5 instance: sinusoidal or piecewise coefficients, Fourier Q."""
+    """One instance of the slab batch: sinusoidal or piecewise coefficients, Fourier Q."""
     x = cell_centres(I)
     if rng.uniform() < 0.5:
         k = rng.integers(1, 5)
@@ -211,7 +211,7 @@ def slab_instance(rng, I, N):
     return Slab1G(I=I, N=N, sigt=sigt, sigs=c * sigt, Q=fourier_source(rng, x))
 
 
-def config5(seed=5, n_inst=4096, I_range=(64, 2048), N_range=(8, 64)):
+def slab_batch(seed=5, n_inst=4096, I_range=(64, 2048), N_range=(8, 64)):
     """4096 independent slabs, I ~ U{64..2048}, N even ~ U{8..64}."""
     rng = np.random.default_rng(seed)
     out = []
