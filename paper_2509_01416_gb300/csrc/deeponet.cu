@@ -2,8 +2,10 @@
 // iteration around it (Sec. 3.1 Eq. 7, Sec. 3.2 Eq. 8, Sec. 5.1 Eq. 24).
 //
 // Network: branch MLP on `sensors` source values, trunk MLP on x/length,
-// output <branch, trunk>; ReLU after hidden layers.  All matrix products run
-// on the BF16 tensor-core GEMM of nn_kernels.cu with FP32 accumulation.
+// output <branch, trunk>; ReLU after hidden layers.  Matrix products run on
+// BF16 tensor cores with FP32 accumulation: the GEMM of nn_kernels.cu in
+// general, the fused recast step (recast_fused.cu) and the tcgen05 trunk
+// evaluation (trunk_tc.cu) for the 128-sensor, 4 x 128, p = 128 network.
 //
 // Recast on a batch of slabs: the operator lives on its own grid of M bins
 // over [0, L]; each instance's source S and mismatch
@@ -14,7 +16,8 @@
 // integral, sigma+- = h sum max(+-src, 0)), giving branch
 // coefficients beta and u_new = T_ref beta with T_ref the trunk at the bin
 // centres.  Converged instances freeze.  The final flux at the instance's own
-// cell centres is beta . trunk(x_c).
+// cell centres is beta . trunk(x_c), with the trunk evaluated once per
+// distinct cell centre of the batch.
 #include <algorithm>
 #include <numeric>
 #include <cmath>
