@@ -212,13 +212,11 @@ __device__ __forceinline__ void sweep_half(const bool block, Cell4<T>* X, Cell2<
 #pragma unroll
     for (int q = 0; q < A; ++q) psi[q].set(psi_bnd[q]);
     if (nt > 1) {
-        // the chunk map's offset B is summed plainly: it only sets the
-        // chunk's inflow, whose rounding the compensated sweep then carries
-        T Bc[A];
+        CSum<T> Bc[A];
         T D[A];
 #pragma unroll
         for (int q = 0; q < A; ++q) {
-            Bc[q] = T(0);
+            Bc[q].set(T(0));
             D[q] = T(0);
         }
 #pragma unroll 1
@@ -242,7 +240,7 @@ __device__ __forceinline__ void sweep_half(const bool block, Cell4<T>* X, Cell2<
                 if constexpr (P1) sq = MINUS ? s - an.mua[q] * s1 : s + an.mua[q] * s1;
                 const T r2 = T(2) * rcp_dd(cc[q] + st);
                 D[q] = (r2 * st) * (T(1) - D[q]) + D[q];
-                Bc[q] += r2 * (sq - st * Bc[q]);
+                Bc[q].add(r2 * (sq - st * Bc[q].hi));
             }
         }
         // inclusive scan of the chunk maps along the sweep (lanes stride ng)
@@ -250,7 +248,7 @@ __device__ __forceinline__ void sweep_half(const bool block, Cell4<T>* X, Cell2<
 #pragma unroll
         for (int q = 0; q < A; ++q) {
             Dv[q] = D[q];
-            Bv[q] = Bc[q];
+            Bv[q] = Bc[q].val();
         }
         for (int d = 1; d < nt; d <<= 1) {
 #pragma unroll
