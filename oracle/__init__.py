@@ -14,6 +14,9 @@ Layout
   neural.py    DeepONet / FNO forward and backward, MSE, Adam (Sec. 4, App. A1)
   recast.py    equation-recast iteration, Eq. 7/8 and Eq. 24, and the
                simple-preconditioning eigen solve (App. A2, Eq. A5-A6)
+  dsa.py       diffusion synthetic acceleration of slab source iteration
+               (a classical accelerator, not the paper's method, kept for
+               comparison with the warm start)
 
 Pins (what fixes each function independently of itself) live in
 ``tests/test_oracle_*.py``; functions without such a pin say "parity unpinned"

@@ -240,15 +240,22 @@ def rel_change(new, old):
 
 
 def source_iteration(prob, quad, src=None, phi0=None, tol=1e-10, itmax=100000,
-                     sweeper=None, history=False):
+                     sweeper=None, history=False, dsa=False):
     """Source iteration (the operator M of Eq. 3a/4b, Eq. 20) to ||dphi||/||phi|| <= tol.
 
     ``src`` is the isotropic source S per group (default prob.Q); ``phi0`` the
-    initial flux (default zero, the plain guess).  Returns SIResult.
+    initial flux (default zero, the plain guess).  ``dsa``: follow each
+    group's sweep by the diffusion synthetic correction of oracle/dsa.py
+    (slabs with isotropic scattering; not part of the paper's method).
+    Returns SIResult.
     """
     S = prob.Q if src is None else src
     G = prob.G
     sw = make_sweeper(prob, quad) if sweeper is None else sweeper
+    if dsa:
+        from . import dsa as D
+        if not isinstance(prob, Slab) or prob.sigs1 is not None:
+            raise ValueError("diffusion synthetic acceleration: isotropic slabs only")
     phi = np.zeros_like(prob.sigt) if phi0 is None else np.array(phi0, float)
     # Eq. 25: the linearly anisotropic part of the emission, (3/2) Sigma_s1 mu J,
     # with the current J of the previous iteration (zero at the start)
@@ -268,6 +275,8 @@ def source_iteration(prob, quad, src=None, phi0=None, tol=1e-10, itmax=100000,
                 phi[g], cur[g] = sw.sweep_p1(g, q, 1.5 * prob.sigs1[g] * cur[g])
             else:
                 phi[g] = sw.sweep(g, q)
+            if dsa:
+                phi[g] = D.correct(prob, g, phi[g], old[g], quad, sw)
         change = rel_change(phi, old)
         if history:
             hist.append(change)
@@ -293,11 +302,12 @@ class EigenResult:
 
 
 def power_iteration(prob, quad, tol_k=1e-10, tol_phi=1e-10, tol_inner=1e-10,
-                    itmax_outer=10000, itmax_inner=100000, phi0=None, k0=1.0):
+                    itmax_outer=10000, itmax_inner=100000, phi0=None, k0=1.0, dsa=False):
     """Power iteration P with inner source iteration M (App. A2, Eq. A2-A4).
 
-    Plain guess: flat flux and k = 1.  Returns EigenResult with phi normalised
-    to unit production.
+    Plain guess: flat flux and k = 1.  ``dsa``: the inner iterations carry
+    the diffusion synthetic correction (see source_iteration).  Returns
+    EigenResult with phi normalised to unit production.
     """
     G = prob.G
     if isinstance(prob, Slab) and prob.sigs1 is not None:
@@ -318,7 +328,7 @@ def power_iteration(prob, quad, tol_k=1e-10, tol_phi=1e-10, tol_inner=1e-10,
         # chi_g F / k for every group, F the production density of each cell
         src = prob.chi.reshape((G,) + (1,) * F.ndim) * F[None] / k
         r = source_iteration(prob, quad, src=src, phi0=phi, tol=tol_inner,
-                             itmax=itmax_inner, sweeper=sw)
+                             itmax=itmax_inner, sweeper=sw, dsa=dsa)
         inner_total += r.iterations
         P = production(prob, r.phi)
         k_new = k * P

@@ -1,0 +1,156 @@
+"""Pins for the oracle's diffusion synthetic acceleration (oracle/dsa.py).
+
+The correction is pinned by what the mathematics fixes independently of the
+code: closed-form solutions of its edge diffusion system, the Fourier
+analysis of diffusion synthetic acceleration in an unbounded medium (the
+error reduction per iteration of the slowest mode), the reduction to source
+iteration without scattering, and the fixed point (the transport answer of
+plain source iteration).
+"""
+import numpy as np
+import pytest
+from scipy.linalg import solve_banded
+
+from oracle import dsa as D
+from oracle import quadrature as Qd
+from oracle import transport as T
+
+
+def _fourier_rate(N, c):
+    """Largest error reduction per iteration over the Fourier modes
+    exp(i lam x) of an unbounded medium with Sigma_t = 1 (continuous in x).
+    The sweep multiplies a mode by s = c sum (w/2) / (1 + lam^2 mu^2); the
+    residual c (s - 1) then drives the diffusion equation, whose symbol is
+    lam^2 / 3 + (1 - c), and its solution is added."""
+    mu, w = Qd.gauss_legendre(N)
+    lam = np.linspace(1e-4, 40.0, 400001)
+    sweep = c * np.sum(0.5 * w[None, :] / (1.0 + (lam[:, None] * mu[None, :]) ** 2), axis=1)
+    # residual c (sweep - 1) phi, diffusion symbol lam^2 / 3 + (1 - c)
+    omega = sweep + c * (sweep - 1.0) / (lam ** 2 / 3.0 + 1.0 - c)
+    return float(np.max(np.abs(omega)))
+
+
+def _measured_rate(h, c, I, N, its=22, seed=0):
+    P = T.uniform_slab(I, h * I, 1.0, c, Q=np.zeros(I))
+    q = Qd.gauss_legendre(N)
+    phi = np.random.default_rng(seed).standard_normal((1, I))
+    norms = [np.linalg.norm(phi)]
+    for _ in range(its):
+        # vacuum faces: no angular state carries over between calls
+        phi = T.source_iteration(P, q, phi0=phi, tol=0.0, itmax=1, dsa=True).phi
+        norms.append(np.linalg.norm(phi))
+    return norms[-1] / norms[-2]
+
+
+def test_edge_system_pure_scatterer_is_a_parabola():
+    # Sigma_a = 0, vacuum faces, uniform residual R on a uniform mesh: the
+    # three-point operator is exact on quadratics, so the edge values are
+    # e(x) = R x (L - x) / (2 D) + R L / (2 a), a the half-range current
+    I, L, R = 37, 3.7, 0.8
+    mu, w = Qd.gauss_legendre(8)
+    a = D.half_range_current(mu, w)
+    P = T.uniform_slab(I, L, 1.3, 1.3, Q=np.zeros(I))
+    e = D.edge_correction(P, 0, np.full(I, R), (mu, w))
+    x = np.linspace(0.0, L, I + 1)
+    Dc = 1.0 / (3.0 * 1.3)
+    assert np.allclose(e, R * x * (L - x) / (2 * Dc) + R * L / (2 * a), rtol=1e-12)
+
+
+def test_edge_system_reflective_absorber_is_flat():
+    # reflective faces, uniform absorber and residual: e = R / Sigma_a
+    I = 25
+    P = T.uniform_slab(I, 2.0, 1.5, 0.9, Q=np.zeros(I),
+                       bc_left=T.REFLECTIVE, bc_right=T.REFLECTIVE)
+    e = D.edge_correction(P, 0, np.full(I, 0.3), Qd.gauss_legendre(4))
+    assert np.allclose(e, 0.3 / 0.6, rtol=1e-12)
+
+
+def test_half_range_current_limit():
+    mu, w = Qd.gauss_legendre(2)
+    assert D.half_range_current(mu, w) == pytest.approx(1 / np.sqrt(3), rel=1e-14)
+    mu, w = Qd.gauss_legendre(128)
+    assert D.half_range_current(mu, w) == pytest.approx(0.5, abs=1e-4)
+
+
+@pytest.mark.parametrize("h,c,I", [(0.01, 0.9, 2000), (0.1, 0.99, 400), (1.0, 0.9, 200)])
+def test_rate_matches_fourier_analysis(h, c, I):
+    # a long vacuum slab of thin or moderate cells behaves like the unbounded
+    # medium: the slowest mode shrinks by the Fourier-analysis factor
+    # (0.2154 c for S16 at c = 0.9, 0.2247 c for S_infinity at c = 1)
+    want = _fourier_rate(16, c)
+    got = _measured_rate(h, c, I, 16)
+    assert got == pytest.approx(want, rel=0.03), (got, want)
+    # and source iteration alone would shrink it by about c
+    assert got < 0.25 * c
+
+
+def test_thick_cells_stay_stable():
+    # the diamond-difference-consistent correction keeps its effect for
+    # cells many mean free paths thick
+    for h in (10.0, 100.0):
+        assert _measured_rate(h, 0.99, 100, 16) < 0.25
+
+
+def test_without_scattering_dsa_is_one_sweep():
+    I = 40
+    rng = np.random.default_rng(3)
+    P = T.uniform_slab(I, 4.0, rng.uniform(0.5, 2.0, I), 0.0, Q=rng.uniform(0, 1, I))
+    q = Qd.gauss_legendre(8)
+    a = T.source_iteration(P, q, tol=0.0, itmax=1).phi
+    b = T.source_iteration(P, q, tol=0.0, itmax=1, dsa=True).phi
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("bcl,bcr", [(T.VACUUM, T.VACUUM), (T.REFLECTIVE, T.VACUUM),
+                                     (T.VACUUM, T.REFLECTIVE)])
+def test_fixed_point_is_the_transport_answer(bcl, bcr):
+    rng = np.random.default_rng(11)
+    I = 120
+    st = rng.uniform(0.5, 3.0, I)
+    P = T.uniform_slab(I, 12.0, st, st * rng.uniform(0.6, 0.98, I),
+                       Q=rng.uniform(0.0, 2.0, I), bc_left=bcl, bc_right=bcr)
+    q = Qd.gauss_legendre(16)
+    si = T.source_iteration(P, q, tol=1e-13, itmax=100000)
+    ac = T.source_iteration(P, q, tol=1e-13, itmax=1000, dsa=True)
+    assert np.linalg.norm(ac.phi - si.phi) / np.linalg.norm(si.phi) < 1e-11
+    assert ac.iterations * 3 < si.iterations
+
+
+def test_two_groups_and_eigen_keep_their_answers():
+    # per-group correction inside the Gauss-Seidel sweep over groups, and
+    # inside the inner iterations of the power iteration
+    rng = np.random.default_rng(5)
+    I = 60
+    dx = np.full(I, 0.1)
+    sigt = np.stack([rng.uniform(0.8, 1.2, I), rng.uniform(1.5, 2.5, I)])
+    sigs = np.zeros((2, 2, I))
+    sigs[0, 0] = 0.6 * sigt[0]
+    sigs[0, 1] = 0.2 * sigt[0]
+    sigs[1, 1] = 0.9 * sigt[1]
+    P = T.Slab(dx=dx, sigt=sigt, sigs=sigs, Q=np.stack([np.ones(I), np.zeros(I)]))
+    q = Qd.gauss_legendre(8)
+    si = T.source_iteration(P, q, tol=1e-13, itmax=100000)
+    ac = T.source_iteration(P, q, tol=1e-13, itmax=1000, dsa=True)
+    assert np.linalg.norm(ac.phi - si.phi) / np.linalg.norm(si.phi) < 1e-11
+    assert ac.iterations < si.iterations
+    E = T.uniform_slab(80, 8.0, 1.0, 0.7, nusigf=0.45)
+    pe = T.power_iteration(E, q, tol_k=1e-11, tol_phi=1e-10, tol_inner=1e-11)
+    de = T.power_iteration(E, q, tol_k=1e-11, tol_phi=1e-10, tol_inner=1e-11, dsa=True)
+    assert abs(pe.k - de.k) < 1e-9
+    assert de.inner_total * 2 < pe.inner_total
+
+
+def test_banded_form_is_the_assembled_matrix():
+    # the banded storage holds the sum of the cell matrices K_i
+    rng = np.random.default_rng(2)
+    I = 6
+    dx, st, sa = rng.uniform(0.1, 1, I), rng.uniform(0.5, 2, I), rng.uniform(0, 0.5, I)
+    ab = D.edge_matrix(dx, st, sa, 0.4, 0.0)
+    K = np.zeros((I + 1, I + 1))
+    for i in range(I):
+        k = (1 / (3 * st[i] * dx[i])) * np.array([[1, -1], [-1, 1]]) + \
+            (sa[i] * dx[i] / 4) * np.ones((2, 2))
+        K[i:i + 2, i:i + 2] += k
+    K[0, 0] += 0.4
+    b = rng.standard_normal(I + 1)
+    assert np.allclose(solve_banded((1, 1), ab, b), np.linalg.solve(K, b), rtol=1e-12)
