@@ -171,6 +171,8 @@ def main():
                          "no training set; for profiling runs)")
     ap.add_argument("--recast-tol", type=float, default=RECAST_TOL)
     ap.add_argument("--recast-itmax", type=int, default=RECAST_ITMAX)
+    ap.add_argument("--no-dsa", action="store_true",
+                    help="skip the diffusion-synthetic-acceleration comparison runs")
     ap.add_argument("--instances", type=int, default=0,
                     help="solve only the first N instances of the batch (profiling aid)")
     args = ap.parse_args()
@@ -225,19 +227,19 @@ def main():
     s.set_slabs(n, wdt, order, sigt, sigs, source=src)
     phi_dev = torch.empty(Ctot, dtype=torch.float64, device="cuda")
 
-    def step(warm=True):
+    def step(warm=True, dsa=False):
         return s.solve_fixed_source_dev(phi_dev.data_ptr(), tol=TOL, itmax=200000,
                                         precision=0, warm_start=1 if warm else 0,
                                         recast_tol=args.recast_tol,
-                                        recast_itmax=args.recast_itmax)
+                                        recast_itmax=args.recast_itmax, dsa=dsa)
 
     def barrier():
         if world > 1:
             dist.barrier()
 
-    def timed(warm, steps, clk=None):
+    def timed(warm, steps, clk=None, dsa=False):
         for _ in range(max(3, args.warmup)):
-            info = step(warm)
+            info = step(warm, dsa)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.set_timing(True)
         barrier()
@@ -249,7 +251,7 @@ def main():
             torch.cuda.profiler.start()
         ev0.record(stream)
         for _ in range(steps):
-            info = step(warm)
+            info = step(warm, dsa)
         ev1.record(stream)
         torch.cuda.synchronize()
         if clk:
@@ -266,6 +268,17 @@ def main():
     ms_max, tm, info = timed(True, args.steps, clk)
     value = whole_job_rate(world, B, args.steps, ms_max / 1e3)
     plain_value = whole_job_rate(world, B, max(1, args.steps // 2), plain_ms / 1e3)
+    # the classical accelerator of the iteration itself on the same batch, alone
+    # and behind the warm start (not part of the headline metric)
+    accel = {}
+    if not args.no_dsa:
+        for key, warm in (("dsa", False), ("warm_start_and_dsa", True)):
+            k = max(1, args.steps // 2)
+            ms_a, _, info_a = timed(warm, k, dsa=True)
+            it_a = info_a["iterations"].astype(np.float64)
+            accel[key] = {"value": whole_job_rate(world, B, k, ms_a / 1e3), "unit": UNIT,
+                          "ms_per_step": ms_a / k, "iterations_mean": float(np.mean(it_a)),
+                          "iterations_max": int(np.max(it_a))}
 
     # ---- end to end through the C ABI with host buffers (warm start): the
     # step's inputs go from pinned host memory to the device and the flux
@@ -348,6 +361,7 @@ def main():
                        "operator_ms_per_step": tm["operator_ms"] / args.steps,
                        "sweep_ms_per_step": tm["sweep_ms"] / args.steps,
                        "speedup_vs_plain": value / plain_value if plain_value else None},
+        "iteration_accelerators": accel or None,
         "training": None if hist is None else
                     {"samples": 2000, "steps": args.train_steps, "batch": 100,
                      "seconds": train_s, "loss_first": float(hist[0]),

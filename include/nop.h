@@ -70,6 +70,19 @@ extern "C" {
 #define NOP_OUT_DEVICE   2 /* phi_out / k_out are device pointers; the call does
                               not synchronise (results valid once the context
                               stream reaches this point)                      */
+#define NOP_DSA          8 /* slabs: follow every group's sweep by a diffusion
+                              synthetic correction (fixed source and the inner
+                              iterations of eigen solves).  A classical
+                              accelerator of the iteration itself, not the
+                              paper's method (which keeps the iteration of
+                              Sec. 3.1 Eq. 3a/4b and improves the first
+                              iterate); the residual Sigma_s,gg (phi^{l+1/2} -
+                              phi^l) drives the P1 equations written with the
+                              sweep's diamond-difference closure, an edge-based
+                              symmetric tridiagonal system per instance and
+                              group, factored once per solve.  The converged
+                              flux is unchanged.  NOP_EINVAL with sigma_s1 or
+                              the x-y geometry.                               */
 
 #define NOP_SCHED_AUTO   0
 #define NOP_SCHED_WARP   1
@@ -133,7 +146,7 @@ typedef struct {
     int warm_start;        /* NOP_WARM_NONE or NOP_WARM_RECAST                 */
     double recast_tol;     /* recast loop tolerance (Eq. 24)                   */
     int recast_itmax;      /* recast loop iteration cap                        */
-    int flags;             /* NOP_PHI0_DEVICE | NOP_OUT_DEVICE                 */
+    int flags;             /* NOP_PHI0_DEVICE | NOP_OUT_DEVICE | NOP_DSA       */
     int schedule;          /* slab batches: NOP_SCHED_AUTO, NOP_SCHED_WARP (one
                               warp per instance), NOP_SCHED_BLOCK (a whole block
                               per instance where the angles allow it)         */

@@ -58,8 +58,10 @@ __all__ = ["Solver", "NopError", "capi"]
 
 def _opts(tol=1e-6, itmax=10000, precision=NOP_PREC_F32, tol_k=1e-7, tol_inner=None,
           itmax_inner=10000, warm_start=NOP_WARM_NONE, recast_tol=1e-4, recast_itmax=200,
-          flags=0, schedule=0):
+          flags=0, schedule=0, dsa=False):
     o = capi.nop_solve_opts()
+    if dsa:
+        flags |= capi.NOP_DSA
     o.tol, o.tol_k = tol, tol_k
     o.tol_inner = tol if tol_inner is None else tol_inner
     o.itmax, o.itmax_inner, o.precision = itmax, itmax_inner, precision

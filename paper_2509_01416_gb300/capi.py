@@ -18,7 +18,7 @@ NOP_GEOM_SLAB, NOP_GEOM_XY = 1, 2
 NOP_BC_VACUUM, NOP_BC_REFLECTIVE = 0, 1
 NOP_PREC_F32, NOP_PREC_F64 = 0, 1
 NOP_WARM_NONE, NOP_WARM_RECAST, NOP_WARM_RECAST_CP = 0, 1, 2
-NOP_PHI0_DEVICE, NOP_OUT_DEVICE, NOP_SP_CONSTRAINED = 1, 2, 4
+NOP_PHI0_DEVICE, NOP_OUT_DEVICE, NOP_SP_CONSTRAINED, NOP_DSA = 1, 2, 4, 8
 NOP_SCHED_AUTO, NOP_SCHED_WARP, NOP_SCHED_BLOCK = 0, 1, 2
 NOP_NOALLOC_MAX_CELLS, NOP_NOALLOC_MAX_ORDER = 65536, 128
 

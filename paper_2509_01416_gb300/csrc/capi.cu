@@ -436,6 +436,11 @@ static int check_opts(nop_ctx* ctx, const nop_solve_opts* o, bool eigen) {
         ctx->set_error("eigen solve needs tol_k, tol_inner > 0 and itmax_inner >= 1");
         return NOP_EINVAL;
     }
+    if ((o->flags & NOP_DSA) && ctx->has_problem &&
+        (ctx->geometry != NOP_GEOM_SLAB || ctx->sigs1_d != nullptr)) {
+        ctx->set_error("diffusion synthetic acceleration: slabs with isotropic scattering only");
+        return NOP_EINVAL;
+    }
     return NOP_OK;
 }
 

@@ -45,6 +45,14 @@ struct alignas(2 * sizeof(T)) Cell2 {
     T s0, s1;
 };
 
+// One edge of the diffusion synthetic acceleration system: the forward
+// elimination y_k = fa y_{k-1} + fm b_k, the back substitution
+// e_k = bc e_{k+1} + y_k, and y (the right-hand side's image, then y_k).
+template <typename T>
+struct alignas(4 * sizeof(T)) DsaEdge {
+    T fa, fm, bc, y;
+};
+
 struct Sn1dArgs {
     int n_inst;
     int G;
@@ -76,6 +84,11 @@ struct Sn1dArgs {
     void* s1buf;          // T [C]: (3/2) Sigma_s1 J of the group being swept
     void* jm;             // T [C]: mu < 0 part of the new current
     int bc_left, bc_right;
+    // diffusion synthetic acceleration: factors of each instance's edge
+    // diffusion system, DsaEdge<T> [G][C + n_inst], instance b's I+1 edges
+    // starting at cell_off[b] + b
+    int dsa;
+    void* dsaf;
     int smem_cells;       // cells the block path can stage in shared memory
     // eigen
     int eigen;
@@ -201,7 +214,8 @@ __device__ __forceinline__ void sweep_half(const bool block, Cell4<T>* X, Cell2<
                                            const Stage<T>& sg, int I, int lg,
                                            const T (&cc)[A], const T (&wt)[A],
                                            const T (&psi_bnd)[A], T (&psi_out)[A],
-                                           T& acc_d, T& acc_n, const P1Op<T, A>& an) {
+                                           T& acc_d, T& acc_n, const P1Op<T, A>& an,
+                                           const bool keep_df) {
     const int lane = threadIdx.x & 31;
     const int ng = 1 << lg, nt = 32 >> lg;
     const int j = lane & (ng - 1), t = lane >> lg;
@@ -326,6 +340,7 @@ __device__ __forceinline__ void sweep_half(const bool block, Cell4<T>* X, Cell2<
                 acc_d += df * df;
                 acc_n += phin * phin;
                 X[i].phi = phin;
+                if (keep_df) U[i].s0 = df;
                 if constexpr (P1) an.jc[i] = pj + an.jm[i];
             }
         }
@@ -350,6 +365,100 @@ __device__ void group_source(const Sn1dArgs& a, const Grp& gr, long long off, in
     }
 }
 
+// Diffusion synthetic correction of group g after its sweep, on one warp.
+// U[i].s0 holds df_i = phi^{l+1/2}_i - phi^l_i.  The edge system (I+1
+// edges, factored by sn1d_dsa_factor) has the load b_k = r_{k-1} + r_k with
+// r_i = (h/2) Sigma_s,i df_i = h X[i].y df_i.  Both triangular solves are
+// affine recurrences along the edges, so each is split into 32 chunks, one
+// per lane: every lane composes its chunk's map, the maps are scanned with
+// shuffles (left to right for the forward elimination, right to left for
+// the back substitution), and the lanes then run their chunks from the
+// correct entry value.  The cell correction (e_k + e_{k+1}) / 2 is added to
+// phi, the change df + correction enters the norms, and a reflective right
+// face's stored outflow (the next sweep's inflow) receives e_I / 2.
+template <typename T>
+__device__ void dsa_pass(const Sn1dArgs& a, int inst, int g, long long off, int I, int h,
+                         T& acc_d, T& acc_n) {
+    const int lane = threadIdx.x & 31;
+    Cell4<T>* X = (Cell4<T>*)a.X + (long long)g * a.C + off;
+    Cell2<T>* U = (Cell2<T>*)a.U + off;
+    DsaEdge<T>* F = (DsaEdge<T>*)a.dsaf + (long long)g * (a.C + a.n_inst) + off + inst;
+    const T hx = (T)a.dx[inst];
+    const int E = I + 1;
+    const int m = (E + 31) / 32;
+    const int k0 = lane * m;
+    const int len = max(0, min(m, E - k0));
+    const int k1 = k0 + len;
+    // forward elimination: compose, keeping fm_k b_k for the second pass
+    T P = T(1), Q = T(0);
+    T rprev = (len > 0 && k0 > 0) ? hx * X[k0 - 1].y * U[k0 - 1].s0 : T(0);
+#pragma unroll 1
+    for (int k = k0; k < k1; ++k) {
+        const DsaEdge<T> f = F[k];
+        const T r = k < I ? hx * X[k].y * U[k].s0 : T(0);
+        const T beta = f.fm * (rprev + r);
+        rprev = r;
+        F[k].y = beta;
+        Q = f.fa * Q + beta;
+        P = f.fa * P;
+    }
+    for (int d = 1; d < 32; d <<= 1) {
+        const T Po = __shfl_up_sync(0xffffffffu, P, d);
+        const T Qo = __shfl_up_sync(0xffffffffu, Q, d);
+        if (lane >= d) {
+            Q = P * Qo + Q;
+            P = P * Po;
+        }
+    }
+    T y = __shfl_up_sync(0xffffffffu, Q, 1);
+    if (lane == 0) y = T(0);
+#pragma unroll 1
+    for (int k = k0; k < k1; ++k) {
+        y = F[k].fa * y + F[k].y;
+        F[k].y = y;
+    }
+    // back substitution, right to left (bc of the last edge is zero)
+    P = T(1);
+    Q = T(0);
+#pragma unroll 1
+    for (int k = k1 - 1; k >= k0; --k) {
+        const DsaEdge<T> f = F[k];
+        Q = f.bc * Q + f.y;
+        P = f.bc * P;
+    }
+    for (int d = 1; d < 32; d <<= 1) {
+        const T Pn = __shfl_down_sync(0xffffffffu, P, d);
+        const T Qn = __shfl_down_sync(0xffffffffu, Q, d);
+        if (lane + d < 32) {
+            Q = P * Qn + Q;
+            P = P * Pn;
+        }
+    }
+    T en = __shfl_down_sync(0xffffffffu, Q, 1);
+    if (lane == 31) en = T(0);
+    T e_last = T(0);
+#pragma unroll 1
+    for (int k = k1 - 1; k >= k0; --k) {
+        const DsaEdge<T> f = F[k];
+        const T e = f.bc * en + f.y;
+        if (k == I) e_last = e;
+        if (k < I) {
+            const T fc = T(0.5) * (e + en);
+            const T pn = X[k].phi + fc;
+            X[k].phi = pn;
+            const T ch = U[k].s0 + fc;
+            acc_d += ch * ch;
+            acc_n += pn * pn;
+        }
+        en = e;
+    }
+    if (a.bc_right) {
+        const T eI = __shfl_sync(0xffffffffu, e_last, I / m);
+        T* PB = (T*)a.psib + a.boff[inst];
+        for (int hi = lane; hi < h; hi += 32) PB[(g * h + hi) * 2 + 1] += T(0.5) * eI;
+    }
+}
+
 // One source iteration over all groups; returns the relative L2 change.
 // [hb, he): this warp's slice of the half-angle range (all of it on the warp
 // path).
@@ -362,6 +471,7 @@ __device__ double si_iteration(const Sn1dArgs& a, const Grp& gr, const Stage<T>&
     T* PB = (T*)a.psib + a.boff[inst];
     T acc_d = T(0), acc_n = T(0);
     for (int g = 0; g < a.G; ++g) {
+        const T keep_d = acc_d, keep_n = acc_n;
         if (a.G > 1) {
             group_source<T>(a, gr, off, I, g);
             gr.sync();
@@ -401,7 +511,7 @@ __device__ double si_iteration(const Sn1dArgs& a, const Grp& gr, const Stage<T>&
         // only joins the barriers
         if (hb < he) {
             sweep_half<T, A, true, P1>(gr.block, X, U, sg, I, lg, cc, wt, bnd, out, acc_d, acc_n,
-                                       an);
+                                       an, false);
             __syncwarp();
 #pragma unroll
             for (int q = 0; q < A; ++q) {
@@ -410,7 +520,7 @@ __device__ double si_iteration(const Sn1dArgs& a, const Grp& gr, const Stage<T>&
                 bnd[q] = a.bc_left ? out[q] : T(0);
             }
             sweep_half<T, A, false, P1>(gr.block, X, U, sg, I, lg, cc, wt, bnd, out, acc_d, acc_n,
-                                        an);
+                                        an, a.dsa != 0);
 #pragma unroll
             for (int q = 0; q < A; ++q) {
                 const int hi = hb + j * A + q;
@@ -426,7 +536,16 @@ __device__ double si_iteration(const Sn1dArgs& a, const Grp& gr, const Stage<T>&
                 acc_d += df * df;
                 acc_n += phin * phin;
                 X[i].phi = phin;
+                if (a.dsa) U[i].s0 = df;
             }
+            gr.sync();
+        }
+        if (a.dsa) {
+            // the change of this group is that of the corrected flux
+            acc_d = keep_d;
+            acc_n = keep_n;
+            if (!gr.block || gr.warp == 0)
+                dsa_pass<T>(a, inst, g, off, I, h, acc_d, acc_n);
             gr.sync();
         }
     }
@@ -734,6 +853,56 @@ __global__ void sn1d_prepare(long long C, int G, const double* sigt, const doubl
     }
 }
 
+// Factors of the diffusion synthetic acceleration system of every (group,
+// instance), one thread each, FP64 Thomas elimination over the I+1 edges.
+// Cell i contributes D_i/h [[1,-1],[-1,1]] + Sigma_a,i h/4 [[1,1],[1,1]] to
+// its two edges (D = 1/(3 Sigma_t), Sigma_a = Sigma_t - Sigma_s,gg); a
+// vacuum face adds the quadrature's half-range current sum_{mu>0} w mu to its
+// edge.  The matrix is symmetric positive definite unless the instance has
+// no absorption and no vacuum face (then source iteration does not converge
+// either); a pivot that is not positive gives a zero factor there.
+template <typename T>
+__global__ void sn1d_dsa_factor(Sn1dArgs a) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= (long long)a.G * a.n_inst) return;
+    const int g = (int)(t / a.n_inst), b = (int)(t % a.n_inst);
+    const int I = a.ncell[b], N = a.nang[b], q0 = a.qoff[b];
+    const double h = a.dx[b];
+    const long long off = a.cell_off[b];
+    const Cell4<T>* X = (const Cell4<T>*)a.X + (long long)g * a.C + off;
+    DsaEdge<T>* F = (DsaEdge<T>*)a.dsaf + (long long)g * (a.C + a.n_inst) + off + b;
+    double hr = 0.0;   // nodes ascend: the upper half has mu > 0
+    for (int n = N / 2; n < N; ++n) hr += a.w[q0 + n] * a.mu[q0 + n];
+    double dl = 0.0, ml = 0.0;       // D/h and Sigma_a h/4 of the cell left of edge k
+    double oprev = 0.0, cprev = 0.0;
+    for (int k = 0; k <= I; ++k) {
+        double d = dl + ml, o = 0.0, dr = 0.0, mr = 0.0;
+        if (k < I) {
+            const double st = (double)X[k].st;
+            const double sa = st - 2.0 * (double)X[k].y;
+            dr = 1.0 / (3.0 * st * h);
+            mr = 0.25 * sa * h;
+            d += dr + mr;
+            o = mr - dr;
+        }
+        if (k == 0 && !a.bc_left) d += hr;
+        if (k == I && !a.bc_right) d += hr;
+        const double piv = d - oprev * cprev;
+        const double mk = piv > 0.0 && isfinite(piv) ? 1.0 / piv : 0.0;
+        const double ck = o * mk;
+        DsaEdge<T> f;
+        f.fa = (T)(-oprev * mk);
+        f.fm = (T)mk;
+        f.bc = (T)(-ck);
+        f.y = T(0);
+        F[k] = f;
+        oprev = o;
+        cprev = ck;
+        dl = dr;
+        ml = mr;
+    }
+}
+
 template <typename T>
 __global__ void sn1d_finish(long long total, const Cell4<T>* X, double* phi) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
@@ -781,6 +950,16 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
         NOP_TRY(ctx->scratch("sn1d_jm", sizeof(T) * C, &p));
         jm = (T*)p;
     }
+    const bool dsa = (o->flags & NOP_DSA) != 0;
+    if (dsa && p1) {
+        ctx->set_error("diffusion synthetic acceleration needs isotropic scattering");
+        return NOP_EINVAL;
+    }
+    void* dsaf = nullptr;
+    if (dsa) {
+        NOP_TRY(ctx->scratch("sn1d_dsa", sizeof(DsaEdge<T>) * (size_t)G * (size_t)(C + B), &p));
+        dsaf = p;
+    }
     NOP_TRY(ctx->scratch("sn1d_k0", sizeof(double) * B, &p));
     double* k0_d = (double*)p;
     NOP_TRY(ctx->scratch("sn1d_int", sizeof(int) * (5 * (size_t)B + 4), &p));
@@ -813,6 +992,8 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
     for (int b = 0; b < B; ++b) {
         const double c = std::min(0.999, std::max(0.2, s.cmax[b]));
         double its = std::min(5000.0, std::max(5.0, std::log(tol_its) / std::log(c)));
+        // the accelerated iteration contracts like about c/4 (Fourier analysis)
+        if (dsa) its = std::max(3.0, std::log(tol_its) / std::log(std::max(0.05, 0.25 * c)));
         if (!eigen && b < (int)s.last_iters.size() && s.last_iters[b] > 0) its = s.last_iters[b];
         cost[b] = (double)s.ncell[b] * s.order[b] * its * G;
         total_cost += cost[b];
@@ -829,6 +1010,8 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
     // warps), which cuts its latency several times at the price of about 1.5x
     // its SM time on one warp (measured on the 4096-slab batch: thresholds
     // of 0.5-1.5x the mean load gave 33-34, 28.8 and 30-33 ms).
+    // the correction runs on one warp: 4 passes over ceil((I+1)/32) edges
+    auto dsa_steps = [&](int b) { return dsa ? 4.0 * ((s.ncell[b] + 32) / 32) * G : 0.0; };
     std::vector<int> cfg(B), small, big;
     std::vector<double> lat(B);
     double lat_sum = 0, big_work = 0, small_work = 0;
@@ -837,7 +1020,7 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
         sn1d_pick_config(s.ncell[b], s.order[b], &lg, &A, p1 || sizeof(T) == 8);
         cfg[b] = (lg << 8) | A;
         const int nt = 32 >> lg;
-        const double steps = (nt > 1 ? 4.0 : 2.0) * ((s.ncell[b] + nt - 1) / nt) * G;
+        const double steps = (nt > 1 ? 4.0 : 2.0) * ((s.ncell[b] + nt - 1) / nt) * G + dsa_steps(b);
         lat[b] = cost[b] / ((double)s.ncell[b] * s.order[b] * G) * steps;
         lat_sum += lat[b];
     }
@@ -860,7 +1043,7 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
             // latency on the block: the same iterations over its lane split
             const int nt = 32 >> lg;
             lat[b] = cost[b] / ((double)s.ncell[b] * s.order[b] * G) *
-                     (nt > 1 ? 4.0 : 2.0) * ((s.ncell[b] + nt - 1) / nt) * G;
+                     ((nt > 1 ? 4.0 : 2.0) * ((s.ncell[b] + nt - 1) / nt) * G + dsa_steps(b));
             big_work += lat[b];
         } else {
             small.push_back(b);
@@ -939,6 +1122,8 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
     a.jm = jm;
     a.bc_left = ctx->bc[0];
     a.bc_right = ctx->bc[1];
+    a.dsa = dsa ? 1 : 0;
+    a.dsaf = dsaf;
     a.eigen = eigen ? 1 : 0;
     a.nsf = nsf;
     a.chi = ctx->chi_d;
@@ -963,6 +1148,14 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
     NOP_CUDA_TRY(ctx, cudaFuncSetAttribute(sn1d_kernel<T>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)SN1D_STAGE_BYTES));
+    if (dsa) {
+        mk = ctx->phase_begin(2);
+        const long long nf = (long long)G * B;
+        sn1d_dsa_factor<T><<<(int)((nf + 127) / 128), 128, 0, ctx->stream>>>(a);
+        NOP_CUDA_TRY(ctx, cudaGetLastError());
+        ctx->phase_end(mk);
+        ctx->count_launch(false);
+    }
     mk = ctx->phase_begin(0);
     sn1d_kernel<T><<<blocks, SN1D_THREADS, smem, ctx->stream>>>(a);
     NOP_CUDA_TRY(ctx, cudaGetLastError());
