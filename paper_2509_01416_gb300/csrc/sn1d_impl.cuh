@@ -45,12 +45,14 @@ struct alignas(2 * sizeof(T)) Cell2 {
     T s0, s1;
 };
 
-// One edge of the diffusion synthetic acceleration system: the forward
-// elimination y_k = fa y_{k-1} + fm b_k, the back substitution
-// e_k = bc e_{k+1} + y_k, and y (the right-hand side's image, then y_k).
+// One edge k of the diffusion synthetic acceleration system: the inverse
+// pivot fm = 1/p_k and the off-diagonal entry o = o_k between edges k and
+// k+1 (zero for the last edge).  The forward elimination is
+// y_k = fm (b_k - o_{k-1} y_{k-1}), the back substitution
+// e_k = y_k - o_k fm e_{k+1}.
 template <typename T>
-struct alignas(4 * sizeof(T)) DsaEdge {
-    T fa, fm, bc, y;
+struct alignas(2 * sizeof(T)) DsaEdge {
+    T fm, o;
 };
 
 struct Sn1dArgs {
@@ -85,10 +87,16 @@ struct Sn1dArgs {
     void* jm;             // T [C]: mu < 0 part of the new current
     int bc_left, bc_right;
     // diffusion synthetic acceleration: factors of each instance's edge
-    // diffusion system, DsaEdge<T> [G][C + n_inst], instance b's I+1 edges
-    // starting at cell_off[b] + b
+    // diffusion system, DsaEdge<T> [G][C + 32 n_inst] ({1/pivot, off-diagonal}
+    // per edge); instance b's region
+    // starts at cell_off[b] + 32 b and holds its I+1 edges lane-interleaved:
+    // with m = ceil((I+1)/32) edges per lane, edge k = t m + j (lane t's j-th)
+    // sits at j * 32 + t, so a warp's accesses to its lanes' j-th edges are
+    // contiguous
     int dsa;
     void* dsaf;
+    void* dsaw;           // T [2 (C + 32 n_inst)]: work values of instances whose
+                          // correction does not fit the shared-memory scratch
     int smem_cells;       // cells the block path can stage in shared memory
     // eigen
     int eigen;
@@ -157,6 +165,8 @@ struct Stage {
     Cell2<T>* ss;   // [cells] or null (unstaged)
     T* part;        // block path: [nwarps][cells]
     int cells;
+    T* scratch;     // shared memory free between sweeps (the correction's work values)
+    int scratch_words;
 };
 
 // Running sum carried along a sweep.  FP32 keeps a compensation term
@@ -369,38 +379,77 @@ __device__ void group_source(const Sn1dArgs& a, const Grp& gr, long long off, in
 // U[i].s0 holds df_i = phi^{l+1/2}_i - phi^l_i.  The edge system (I+1
 // edges, factored by sn1d_dsa_factor) has the load b_k = r_{k-1} + r_k with
 // r_i = (h/2) Sigma_s,i df_i = h X[i].y df_i.  Both triangular solves are
-// affine recurrences along the edges, so each is split into 32 chunks, one
-// per lane: every lane composes its chunk's map, the maps are scanned with
-// shuffles (left to right for the forward elimination, right to left for
-// the back substitution), and the lanes then run their chunks from the
-// correct entry value.  The cell correction (e_k + e_{k+1}) / 2 is added to
-// phi, the change df + correction enters the norms, and a reflective right
-// face's stored outflow (the next sweep's inflow) receives e_I / 2.
+// affine recurrences along the edges, so the edges are split into 32
+// chunks of m, one per lane, and solved in three passes with a shuffle scan
+// before each of the last two:
+//   1. compose the chunk's forward map y_out = P y_in + Q, keeping fm_k b_k;
+//   2. from the scanned entry value run the forward elimination, keeping
+//      y_k, and compose the chunk's backward map e_first = P e_in + Q
+//      (left to right: Q += (product of the coefficients so far) y_k);
+//   3. from the scanned (right to left) entry value run the back
+//      substitution, add the cell correction (e_k + e_{k+1}) / 2 to phi and
+//      form the change df + correction for the norms.
+// The one work value per edge (fm b, then y) lives in shared memory where it
+// fits (the staging slab, free between sweeps), else in global memory, with
+// a row pitch of 33 (lane t's j-th edge at j * 33 + t: conflict-free).
+// Each pass loads DSA_BATCH edges before their dependent arithmetic.  A
+// reflective right face's stored outflow (the next sweep's inflow) receives
+// e_I / 2.
+#define DSA_BATCH 8
 template <typename T>
-__device__ void dsa_pass(const Sn1dArgs& a, int inst, int g, long long off, int I, int h,
-                         T& acc_d, T& acc_n) {
+__device__ void dsa_pass(const Sn1dArgs& a, const Stage<T>& sg, int inst, int g, long long off,
+                         int I, int h, T& acc_d, T& acc_n) {
     const int lane = threadIdx.x & 31;
     Cell4<T>* X = (Cell4<T>*)a.X + (long long)g * a.C + off;
     Cell2<T>* U = (Cell2<T>*)a.U + off;
-    DsaEdge<T>* F = (DsaEdge<T>*)a.dsaf + (long long)g * (a.C + a.n_inst) + off + inst;
-    const T hx = (T)a.dx[inst];
     const int E = I + 1;
     const int m = (E + 31) / 32;
     const int k0 = lane * m;
-    const int len = max(0, min(m, E - k0));
-    const int k1 = k0 + len;
-    // forward elimination: compose, keeping fm_k b_k for the second pass
-    T P = T(1), Q = T(0);
-    T rprev = (len > 0 && k0 > 0) ? hx * X[k0 - 1].y * U[k0 - 1].s0 : T(0);
+    const int n = max(0, min(m, E - k0));
+    // this lane's factors, lane-interleaved: F[j * 32] is edge k0 + j
+    const DsaEdge<T>* F = (const DsaEdge<T>*)a.dsaf + (long long)g * (a.C + 32LL * a.n_inst) +
+                          off + 32LL * inst + lane;
+    T* W = (sg.scratch && 33 * m <= sg.scratch_words)
+               ? sg.scratch
+               : (T*)a.dsaw + 2 * (off + 32LL * inst);
+    T* Wl = W + lane;   // Wl[j * 33]: edge k0 + j
+    const T hx = (T)a.dx[inst];
+    // the previous lane's last edge: its off-diagonal entry and its cell's r
+    T o_in = T(0), r_in = T(0);
+    if (n > 0 && k0 > 0) {
+        o_in = F[(m - 1) * 32 - 1].o;
+        r_in = hx * X[k0 - 1].y * U[k0 - 1].s0;
+    }
+    // 1. forward map of the chunk
+    T P = T(1), Q = T(0), rprev = r_in, oprev = o_in;
 #pragma unroll 1
-    for (int k = k0; k < k1; ++k) {
-        const DsaEdge<T> f = F[k];
-        const T r = k < I ? hx * X[k].y * U[k].s0 : T(0);
-        const T beta = f.fm * (rprev + r);
-        rprev = r;
-        F[k].y = beta;
-        Q = f.fa * Q + beta;
-        P = f.fa * P;
+    for (int jb = 0; jb < n; jb += DSA_BATCH) {
+        T fm[DSA_BATCH], o[DSA_BATCH], r[DSA_BATCH];
+#pragma unroll
+        for (int q = 0; q < DSA_BATCH; ++q) {
+            const int j = jb + q;
+            fm[q] = T(0);
+            o[q] = T(0);
+            r[q] = T(0);
+            if (j < n) {
+                const DsaEdge<T> f = F[j * 32];
+                fm[q] = f.fm;
+                o[q] = f.o;
+                if (k0 + j < I) r[q] = hx * X[k0 + j].y * U[k0 + j].s0;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < DSA_BATCH; ++q) {
+            if (jb + q < n) {
+                const T fa = -oprev * fm[q];
+                const T beta = fm[q] * (rprev + r[q]);
+                Wl[(jb + q) * 33] = beta;
+                Q = fa * Q + beta;
+                P = fa * P;
+                rprev = r[q];
+                oprev = o[q];
+            }
+        }
     }
     for (int d = 1; d < 32; d <<= 1) {
         const T Po = __shfl_up_sync(0xffffffffu, P, d);
@@ -412,51 +461,92 @@ __device__ void dsa_pass(const Sn1dArgs& a, int inst, int g, long long off, int 
     }
     T y = __shfl_up_sync(0xffffffffu, Q, 1);
     if (lane == 0) y = T(0);
+    // 2. forward elimination and the backward map of the chunk
+    T Pb = T(1), Qb = T(0);
+    oprev = o_in;
 #pragma unroll 1
-    for (int k = k0; k < k1; ++k) {
-        y = F[k].fa * y + F[k].y;
-        F[k].y = y;
-    }
-    // back substitution, right to left (bc of the last edge is zero)
-    P = T(1);
-    Q = T(0);
-#pragma unroll 1
-    for (int k = k1 - 1; k >= k0; --k) {
-        const DsaEdge<T> f = F[k];
-        Q = f.bc * Q + f.y;
-        P = f.bc * P;
+    for (int jb = 0; jb < n; jb += DSA_BATCH) {
+        T fm[DSA_BATCH], o[DSA_BATCH], be[DSA_BATCH];
+#pragma unroll
+        for (int q = 0; q < DSA_BATCH; ++q) {
+            const int j = jb + q;
+            fm[q] = T(0);
+            o[q] = T(0);
+            be[q] = T(0);
+            if (j < n) {
+                const DsaEdge<T> f = F[j * 32];
+                fm[q] = f.fm;
+                o[q] = f.o;
+                be[q] = Wl[j * 33];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < DSA_BATCH; ++q) {
+            if (jb + q < n) {
+                y = -oprev * fm[q] * y + be[q];
+                Wl[(jb + q) * 33] = y;
+                Qb = Pb * y + Qb;
+                Pb = -o[q] * fm[q] * Pb;
+                oprev = o[q];
+            }
+        }
     }
     for (int d = 1; d < 32; d <<= 1) {
-        const T Pn = __shfl_down_sync(0xffffffffu, P, d);
-        const T Qn = __shfl_down_sync(0xffffffffu, Q, d);
+        const T Pn = __shfl_down_sync(0xffffffffu, Pb, d);
+        const T Qn = __shfl_down_sync(0xffffffffu, Qb, d);
         if (lane + d < 32) {
-            Q = P * Qn + Q;
-            P = P * Pn;
+            Qb = Pb * Qn + Qb;
+            Pb = Pb * Pn;
         }
     }
-    T en = __shfl_down_sync(0xffffffffu, Q, 1);
+    T en = __shfl_down_sync(0xffffffffu, Qb, 1);
     if (lane == 31) en = T(0);
+    // 3. back substitution and the correction of the cells, right to left
     T e_last = T(0);
 #pragma unroll 1
-    for (int k = k1 - 1; k >= k0; --k) {
-        const DsaEdge<T> f = F[k];
-        const T e = f.bc * en + f.y;
-        if (k == I) e_last = e;
-        if (k < I) {
-            const T fc = T(0.5) * (e + en);
-            const T pn = X[k].phi + fc;
-            X[k].phi = pn;
-            const T ch = U[k].s0 + fc;
-            acc_d += ch * ch;
-            acc_n += pn * pn;
+    for (int jt = n - 1; jt >= 0; jt -= DSA_BATCH) {
+        T bc[DSA_BATCH], yy[DSA_BATCH], ph[DSA_BATCH], df[DSA_BATCH];
+#pragma unroll
+        for (int q = 0; q < DSA_BATCH; ++q) {
+            const int j = jt - q;
+            bc[q] = T(0);
+            yy[q] = T(0);
+            ph[q] = T(0);
+            df[q] = T(0);
+            if (j >= 0) {
+                const DsaEdge<T> f = F[j * 32];
+                bc[q] = -f.o * f.fm;
+                yy[q] = Wl[j * 33];
+                if (k0 + j < I) {
+                    ph[q] = X[k0 + j].phi;
+                    df[q] = U[k0 + j].s0;
+                }
+            }
         }
-        en = e;
+#pragma unroll
+        for (int q = 0; q < DSA_BATCH; ++q) {
+            const int k = k0 + jt - q;
+            if (jt - q >= 0) {
+                const T e = bc[q] * en + yy[q];
+                if (k == I) e_last = e;
+                if (k < I) {
+                    const T fc = T(0.5) * (e + en);
+                    const T pn = ph[q] + fc;
+                    X[k].phi = pn;
+                    const T ch = df[q] + fc;
+                    acc_d += ch * ch;
+                    acc_n += pn * pn;
+                }
+                en = e;
+            }
+        }
     }
     if (a.bc_right) {
         const T eI = __shfl_sync(0xffffffffu, e_last, I / m);
         T* PB = (T*)a.psib + a.boff[inst];
         for (int hi = lane; hi < h; hi += 32) PB[(g * h + hi) * 2 + 1] += T(0.5) * eI;
     }
+    __syncwarp();
 }
 
 // One source iteration over all groups; returns the relative L2 change.
@@ -545,7 +635,7 @@ __device__ double si_iteration(const Sn1dArgs& a, const Grp& gr, const Stage<T>&
             acc_d = keep_d;
             acc_n = keep_n;
             if (!gr.block || gr.warp == 0)
-                dsa_pass<T>(a, inst, g, off, I, h, acc_d, acc_n);
+                dsa_pass<T>(a, sg, inst, g, off, I, h, acc_d, acc_n);
             gr.sync();
         }
     }
@@ -763,6 +853,9 @@ __device__ void drain_big(const Sn1dArgs& a, double* red, int* job, unsigned cha
     sg.ss = (Cell2<T>*)smem_raw;
     sg.cells = a.smem_cells;
     sg.part = (T*)(sg.ss + a.smem_cells);
+    // between sweeps the whole staging area is free for one warp's correction
+    sg.scratch = (T*)smem_raw;
+    sg.scratch_words = SN1D_STAGE_BYTES / (int)sizeof(T);
     Grp gb;
     gb.block = true;
     gb.rank = threadIdx.x;
@@ -815,6 +908,9 @@ __global__ void __launch_bounds__(SN1D_THREADS, SN1D_BLOCKS_PER_SM) sn1d_kernel(
                     : nullptr;
         sw.part = nullptr;
         sw.cells = slab;
+        // the warp's slab, free between sweeps, holds its correction's work values
+        sw.scratch = (T*)((Cell2<T>*)smem_raw + (threadIdx.x >> 5) * slab);
+        sw.scratch_words = slab * 2;
         dispatch<T>(a, gw, sw, inst);
     }
     if (a.n_big > 0 && !big_first) {
@@ -854,52 +950,160 @@ __global__ void sn1d_prepare(long long C, int G, const double* sigt, const doubl
 }
 
 // Factors of the diffusion synthetic acceleration system of every (group,
-// instance), one thread each, FP64 Thomas elimination over the I+1 edges.
-// Cell i contributes D_i/h [[1,-1],[-1,1]] + Sigma_a,i h/4 [[1,1],[1,1]] to
-// its two edges (D = 1/(3 Sigma_t), Sigma_a = Sigma_t - Sigma_s,gg); a
-// vacuum face adds the quadrature's half-range current sum_{mu>0} w mu to its
-// edge.  The matrix is symmetric positive definite unless the instance has
+// instance), one warp each.  Cell i contributes D_i/h [[1,-1],[-1,1]] +
+// Sigma_a,i h/4 [[1,1],[1,1]] to its two edges (D = 1/(3 Sigma_t),
+// Sigma_a = Sigma_t - Sigma_s,gg); a vacuum face adds the quadrature's
+// half-range current sum_{mu>0} w mu to its edge.  With o_i = Sigma_a,i h/4 -
+// D_i/h the off-diagonal entry of cell i, each diagonal entry is
+// d_k = |o_{k-1}| + |o_k| + delta_k with delta_k = 2 sum over the edge's cells
+// of min(D_i/h, Sigma_a,i h/4) (+ face term) >= 0, and the Thomas pivots are
+// carried as p_k = |o_k| + t_k with
+//     t_0 = delta_0,   t_k = delta_k + |o_{k-1}| t_{k-1} / (|o_{k-1}| + t_{k-1}),
+// a recurrence of positive terms.  (The textbook form p_k = d_k - o_{k-1}^2 /
+// p_{k-1} subtracts nearly equal numbers when the cells are optically thin
+// and loses the absorption in FP32.)  Each step is a Moebius map of t with
+// the positive matrix [[delta + |o|, delta |o|], [1, |o|]], so the lanes
+// compose their chunks' matrices (normalised by the largest entry), scan
+// them with shuffles, and then run their chunks from the scanned entry
+// value.  The matrix is symmetric positive definite unless the instance has
 // no absorption and no vacuum face (then source iteration does not converge
 // either); a pivot that is not positive gives a zero factor there.
 template <typename T>
+__device__ __forceinline__ T dsa_rcp(T x) {
+    return rcp_dd(x);
+}
+
+template <typename T>
+__device__ __forceinline__ void dsa_cell(const Cell4<T>& v, T h, T& o, T& mn) {
+    const T dh = dsa_rcp(T(3) * v.st * h);
+    const T ms = T(0.25) * (v.st - T(2) * v.y) * h;
+    o = ms - dh;
+    mn = fmin(dh, ms);
+}
+
+template <typename T>
+__device__ __forceinline__ void mat_norm(T& a00, T& a01, T& a10, T& a11) {
+    const T mx = fmax(fmax(a00, a01), fmax(a10, a11));
+    if (mx > T(0)) {
+        const T r = dsa_rcp(mx);
+        a00 *= r;
+        a01 *= r;
+        a10 *= r;
+        a11 *= r;
+    }
+}
+
+#define DSA_FACTOR_BATCH 8
+template <typename T>
 __global__ void sn1d_dsa_factor(Sn1dArgs a) {
-    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t >= (long long)a.G * a.n_inst) return;
-    const int g = (int)(t / a.n_inst), b = (int)(t % a.n_inst);
+    const int lane = threadIdx.x & 31;
+    const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    if (wid >= (long long)a.G * a.n_inst) return;   // the whole warp leaves together
+    const int g = (int)(wid / a.n_inst), b = (int)(wid % a.n_inst);
     const int I = a.ncell[b], N = a.nang[b], q0 = a.qoff[b];
-    const double h = a.dx[b];
+    const T h = (T)a.dx[b];
     const long long off = a.cell_off[b];
     const Cell4<T>* X = (const Cell4<T>*)a.X + (long long)g * a.C + off;
-    DsaEdge<T>* F = (DsaEdge<T>*)a.dsaf + (long long)g * (a.C + a.n_inst) + off + b;
-    double hr = 0.0;   // nodes ascend: the upper half has mu > 0
-    for (int n = N / 2; n < N; ++n) hr += a.w[q0 + n] * a.mu[q0 + n];
-    double dl = 0.0, ml = 0.0;       // D/h and Sigma_a h/4 of the cell left of edge k
-    double oprev = 0.0, cprev = 0.0;
-    for (int k = 0; k <= I; ++k) {
-        double d = dl + ml, o = 0.0, dr = 0.0, mr = 0.0;
-        if (k < I) {
-            const double st = (double)X[k].st;
-            const double sa = st - 2.0 * (double)X[k].y;
-            dr = 1.0 / (3.0 * st * h);
-            mr = 0.25 * sa * h;
-            d += dr + mr;
-            o = mr - dr;
+    const int E = I + 1;
+    const int m = (E + 31) / 32;
+    const int k0 = lane * m;
+    const int n = max(0, min(m, E - k0));
+    DsaEdge<T>* F = (DsaEdge<T>*)a.dsaf + (long long)g * (a.C + 32LL * a.n_inst) + off +
+                    32LL * b + lane;
+    // half-range current (nodes ascend: the upper half has mu > 0)
+    double hs = 0.0;
+    for (int q = N / 2 + lane; q < N; q += 32) hs += a.w[q0 + q] * a.mu[q0 + q];
+    const T hr = (T)warp_sum(hs);
+    const T aL = a.bc_left ? T(0) : hr, aR = a.bc_right ? T(0) : hr;
+    T o_in = T(0), mn_in = T(0);
+    if (n > 0 && k0 > 0) dsa_cell<T>(X[k0 - 1], h, o_in, mn_in);
+    // compose this chunk's maps
+    T a00 = T(1), a01 = T(0), a10 = T(0), a11 = T(1);
+    T oprev = o_in, mnprev = mn_in;
+#pragma unroll 1
+    for (int jb = 0; jb < n; jb += DSA_FACTOR_BATCH) {
+        Cell4<T> v[DSA_FACTOR_BATCH];
+#pragma unroll
+        for (int q = 0; q < DSA_FACTOR_BATCH; ++q)
+            if (jb + q < n && k0 + jb + q < I) v[q] = X[k0 + jb + q];
+#pragma unroll
+        for (int q = 0; q < DSA_FACTOR_BATCH; ++q) {
+            const int k = k0 + jb + q;
+            if (jb + q < n) {
+                T o = T(0), mn = T(0);
+                if (k < I) dsa_cell<T>(v[q], h, o, mn);
+                const T delta = T(2) * (mnprev + mn) + (k == 0 ? aL : T(0)) + (k == I ? aR : T(0));
+                T m00, m01, m10, m11;
+                if (k == 0) {
+                    m00 = T(0);
+                    m01 = delta;
+                    m10 = T(0);
+                    m11 = T(1);
+                } else {
+                    const T ao = fabs(oprev);
+                    m00 = delta + ao;
+                    m01 = delta * ao;
+                    m10 = T(1);
+                    m11 = ao;
+                }
+                const T b00 = m00 * a00 + m01 * a10, b01 = m00 * a01 + m01 * a11;
+                const T b10 = m10 * a00 + m11 * a10, b11 = m10 * a01 + m11 * a11;
+                a00 = b00;
+                a01 = b01;
+                a10 = b10;
+                a11 = b11;
+                mat_norm(a00, a01, a10, a11);
+                oprev = o;
+                mnprev = mn;
+            }
         }
-        if (k == 0 && !a.bc_left) d += hr;
-        if (k == I && !a.bc_right) d += hr;
-        const double piv = d - oprev * cprev;
-        const double mk = piv > 0.0 && isfinite(piv) ? 1.0 / piv : 0.0;
-        const double ck = o * mk;
-        DsaEdge<T> f;
-        f.fa = (T)(-oprev * mk);
-        f.fm = (T)mk;
-        f.bc = (T)(-ck);
-        f.y = T(0);
-        F[k] = f;
-        oprev = o;
-        cprev = ck;
-        dl = dr;
-        ml = mr;
+    }
+    // inclusive scan: later chunks' maps act after earlier ones
+    for (int d = 1; d < 32; d <<= 1) {
+        const T c00 = __shfl_up_sync(0xffffffffu, a00, d);
+        const T c01 = __shfl_up_sync(0xffffffffu, a01, d);
+        const T c10 = __shfl_up_sync(0xffffffffu, a10, d);
+        const T c11 = __shfl_up_sync(0xffffffffu, a11, d);
+        if (lane >= d) {
+            const T b00 = a00 * c00 + a01 * c10, b01 = a00 * c01 + a01 * c11;
+            const T b10 = a10 * c00 + a11 * c10, b11 = a10 * c01 + a11 * c11;
+            a00 = b00;
+            a01 = b01;
+            a10 = b10;
+            a11 = b11;
+            mat_norm(a00, a01, a10, a11);
+        }
+    }
+    // t entering this chunk: the earlier chunks' map applied to (0, 1)
+    const T e01 = __shfl_up_sync(0xffffffffu, a01, 1);
+    const T e11 = __shfl_up_sync(0xffffffffu, a11, 1);
+    T t = (lane > 0 && e11 > T(0)) ? e01 / e11 : T(0);
+    oprev = o_in;
+    mnprev = mn_in;
+#pragma unroll 1
+    for (int jb = 0; jb < n; jb += DSA_FACTOR_BATCH) {
+        Cell4<T> v[DSA_FACTOR_BATCH];
+#pragma unroll
+        for (int q = 0; q < DSA_FACTOR_BATCH; ++q)
+            if (jb + q < n && k0 + jb + q < I) v[q] = X[k0 + jb + q];
+#pragma unroll
+        for (int q = 0; q < DSA_FACTOR_BATCH; ++q) {
+            const int k = k0 + jb + q;
+            if (jb + q < n) {
+                T o = T(0), mn = T(0);
+                if (k < I) dsa_cell<T>(v[q], h, o, mn);
+                const T delta = T(2) * (mnprev + mn) + (k == 0 ? aL : T(0)) + (k == I ? aR : T(0));
+                const T ao = fabs(oprev);
+                t = k == 0 ? delta : delta + ao * t * dsa_rcp(ao + t);
+                const T piv = fabs(o) + t;
+                DsaEdge<T> f;
+                f.fm = piv > T(0) && isfinite(piv) ? dsa_rcp(piv) : T(0);
+                f.o = o;
+                F[(jb + q) * 32] = f;
+                oprev = o;
+                mnprev = mn;
+            }
+        }
     }
 }
 
@@ -956,9 +1160,13 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
         return NOP_EINVAL;
     }
     void* dsaf = nullptr;
+    void* dsaw = nullptr;
     if (dsa) {
-        NOP_TRY(ctx->scratch("sn1d_dsa", sizeof(DsaEdge<T>) * (size_t)G * (size_t)(C + B), &p));
+        NOP_TRY(ctx->scratch("sn1d_dsa", sizeof(DsaEdge<T>) * (size_t)G * (size_t)(C + 32LL * B),
+                             &p));
         dsaf = p;
+        NOP_TRY(ctx->scratch("sn1d_dsaw", sizeof(T) * 2 * (size_t)(C + 32LL * B), &p));
+        dsaw = p;
     }
     NOP_TRY(ctx->scratch("sn1d_k0", sizeof(double) * B, &p));
     double* k0_d = (double*)p;
@@ -1124,6 +1332,7 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
     a.bc_right = ctx->bc[1];
     a.dsa = dsa ? 1 : 0;
     a.dsaf = dsaf;
+    a.dsaw = dsaw;
     a.eigen = eigen ? 1 : 0;
     a.nsf = nsf;
     a.chi = ctx->chi_d;
@@ -1150,8 +1359,8 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
                                            (int)SN1D_STAGE_BYTES));
     if (dsa) {
         mk = ctx->phase_begin(2);
-        const long long nf = (long long)G * B;
-        sn1d_dsa_factor<T><<<(int)((nf + 127) / 128), 128, 0, ctx->stream>>>(a);
+        const long long nf = (long long)G * B;   // one warp each
+        sn1d_dsa_factor<T><<<(int)((nf + 3) / 4), 128, 0, ctx->stream>>>(a);
         NOP_CUDA_TRY(ctx, cudaGetLastError());
         ctx->phase_end(mk);
         ctx->count_launch(false);
