@@ -344,7 +344,10 @@ int nop_set_problem(nop_ctx* ctx, const nop_problem* p) {
                                  std::equal(s.ncell.begin(), s.ncell.end(), p->n_cells) &&
                                  std::equal(s.order.begin(), s.order.end(), p->order) &&
                                  (int)s.last_iters.size() == B;
-        if (!same_layout) s.last_iters.assign(B, 0);
+        if (!same_layout) {
+            s.last_iters.assign(B, 0);
+            s.last_iters_dsa.assign(B, 0);
+        }
         s.n_inst = B;
         s.C = C;
         s.ncell.assign(p->n_cells, p->n_cells + B);

@@ -55,6 +55,7 @@ struct SlabDev {
     std::vector<double> width;
     std::vector<double> cmax;        // host: largest in-group scattering ratio
     std::vector<int> last_iters;     // host: iterations of each instance in the last solve
+    std::vector<int> last_iters_dsa; // the same for solves with the diffusion correction
                                      // of this batch layout (0 = unknown); the scheduler's cost
     std::vector<long long> cell_off; // host prefix sums
     long long* cell_off_d = nullptr;

@@ -1195,6 +1195,9 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
     // in-group scattering ratio c (source iteration contracts roughly like c).
     const int blocks_max = ctx->sm_count * SN1D_BLOCKS_PER_SM;
     const double tol_its = eigen ? std::min(o->tol_inner, o->tol) : o->tol;
+    // iterations of the previous solve of this layout, kept apart for solves
+    // with and without the diffusion correction (they differ several times)
+    std::vector<int>& last = dsa ? s.last_iters_dsa : s.last_iters;
     std::vector<double> cost(B);
     double total_cost = 0;
     for (int b = 0; b < B; ++b) {
@@ -1202,7 +1205,7 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
         double its = std::min(5000.0, std::max(5.0, std::log(tol_its) / std::log(c)));
         // the accelerated iteration contracts like about c/4 (Fourier analysis)
         if (dsa) its = std::max(3.0, std::log(tol_its) / std::log(std::max(0.05, 0.25 * c)));
-        if (!eigen && b < (int)s.last_iters.size() && s.last_iters[b] > 0) its = s.last_iters[b];
+        if (!eigen && b < (int)last.size() && last[b] > 0) its = last[b];
         cost[b] = (double)s.ncell[b] * s.order[b] * its * G;
         total_cost += cost[b];
     }
@@ -1437,8 +1440,8 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
         st->max_outer = 0;
         st->max_change = 0;
     }
-    if (!eigen && (int)s.last_iters.size() == B)
-        for (int b = 0; b < B; ++b) s.last_iters[b] = it_h[b];
+    if (!eigen && (int)last.size() == B)
+        for (int b = 0; b < B; ++b) last[b] = it_h[b];
     for (int b = 0; b < B; ++b) {
         if (ctx->timing)
             ctx->cell_angle_updates += (double)it_h[b] * s.ncell[b] * s.order[b] * G;
