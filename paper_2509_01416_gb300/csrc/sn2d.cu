@@ -77,12 +77,37 @@ __global__ void __launch_bounds__(MAXN) xy_sweep_kernel(XYArgs<T> a) {
     if (t < ny && rx) xh = a.out_x[(gx + a.mir_x[d]) * ny + jp];
     __syncthreads();
     const T* st = a.sigt + (long long)a.g * nx * ny;
-    for (int s = 0; s < nx + ny - 1; ++s) {
+    // The cell operands (sigma_t, q) of step s are loaded PF steps ahead, so
+    // their latency hides behind the steps in between instead of stalling
+    // every step of the wavefront.
+    constexpr int PF = 4;
+    const int S = nx + ny - 1;
+    T sgr[PF], qr[PF];
+    auto fetch = [&](int s, T& sg, T& qq) {
+        const int i = s - t;
+        if (t < ny && i >= 0 && i < nx) {
+            const long long c = (long long)jp * nx + (xp ? i : nx - 1 - i);
+            sg = st[c];
+            qq = a.q[c];
+        }
+    };
+#pragma unroll
+    for (int p = 0; p < PF; ++p) {
+        sgr[p] = T(1);
+        qr[p] = T(0);
+        fetch(p, sgr[p], qr[p]);
+    }
+    for (int s0 = 0; s0 < S; s0 += PF)
+#pragma unroll
+    for (int p = 0; p < PF; ++p) {
+        const int s = s0 + p;
+        if (s >= S) break;     // uniform over the block
+        const T sg = sgr[p], qq = qr[p];
+        fetch(s + PF, sgr[p], qr[p]);
         const int i = s - t;   // column in sweep order
         if (t < ny && i >= 0 && i < nx) {
             const int ip = xp ? i : nx - 1 - i;
             const long long c = (long long)jp * nx + ip;
-            const T sg = st[c], qq = a.q[c];
             const T yh = yhi[i], yl = ylo[i];
             const T r = rcp2(sg + cx + cy);
             const T dxs = (qq + cy * yh - (sg + cy) * xh) * r;   // psi_c - psi_x
