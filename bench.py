@@ -171,6 +171,8 @@ def main():
                          "no training set; for profiling runs)")
     ap.add_argument("--recast-tol", type=float, default=RECAST_TOL)
     ap.add_argument("--recast-itmax", type=int, default=RECAST_ITMAX)
+    ap.add_argument("--xy-sweep", action="store_true",
+                    help="profiling aid: time a fixed amount of x-y sweep work instead")
     ap.add_argument("--no-dsa", action="store_true",
                     help="skip the diffusion-synthetic-acceleration comparison runs")
     ap.add_argument("--instances", type=int, default=0,
@@ -187,6 +189,9 @@ def main():
         if rank != 0:
             return
         run_reference(args, insts, world)
+        return
+    if args.xy_sweep:
+        run_xy_sweep(local)
         return
 
     # the oracle's process pool starts before the first GPU call
@@ -390,6 +395,45 @@ def main():
     s.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_xy_sweep(local):
+    """Profiling aid, not the headline: a fixed amount of x-y work (the 256x256
+    8-group checkerboard eigenproblem, 2 outer x 5 inner source iterations)
+    timed with CUDA events after a warm-up solve; the timed solve is bracketed
+    with cudaProfilerStart/Stop.  Prints one JSON line."""
+    import torch
+    from paper_2509_01416_gb300 import Solver
+    torch.cuda.set_device(local)
+    c = W.checkerboard_xy_8g()
+    bc = tuple(c.bc[f] for f in ("x0", "xL", "y0", "yL"))
+    stream = torch.cuda.Stream()
+    s = Solver(local)
+    s.set_stream(stream.cuda_stream)
+    s.set_xy(c.nx, c.ny, c.Lx, c.Ly, c.sigt.reshape(-1), c.sigs.reshape(-1),
+             nu_sigma_f=c.nusigf.reshape(-1), chi=c.chi, bc=bc)
+    kw = dict(tol=1e-12, tol_k=1e-12, tol_inner=1e-12, itmax=2, itmax_inner=5, check=False)
+    s.solve_eigen(**kw)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.set_timing(True)
+    torch.cuda.profiler.start()
+    ev0.record(stream)
+    _, _, info = s.solve_eigen(**kw)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    tm = s.timing()
+    s.set_timing(False)
+    ms = ev0.elapsed_time(ev1)
+    inner = int(np.max(info["inner"]))
+    upd = c.nx * c.ny * 40 * c.sigt.shape[0] * inner
+    print(json.dumps({"metric": "x-y sweep cell-direction-group updates per second",
+                      "value": upd / (ms / 1e3), "unit": "updates/s", "ms": ms,
+                      "sweep_phase_ms": tm["sweep_ms"], "inner_iterations": inner,
+                      "outer_iterations": int(info["outer"]), "launches": int(tm["launches"]),
+                      "config": {"workload": "checkerboard_xy_8g: 256x256, 8 groups, LS S8"}}))
+    s.close()
 
 
 def run_reference(args, insts, world):
