@@ -48,6 +48,7 @@ extern "C" {
 #define NOP_ETIMEOUT  -6   /* a device-side wait hit its limit                  */
 #define NOP_ENAN      -7   /* a non-finite value appeared in a norm             */
 #define NOP_ESTATE    -8   /* call out of order (e.g. solve before set_problem) */
+#define NOP_EIO       -9   /* a file could not be read or written, or is malformed */
 
 /* ------------------------------------------------------------ enumerations */
 #define NOP_GEOM_SLAB  1   /* batch of independent 1D slabs                  */
@@ -286,6 +287,27 @@ int nop_no_set(nop_ctx *ctx, const nop_no_config *cfg, const float *params);
 
 /* Copy the current parameters into a host array of nop_no_param_count entries. */
 int nop_no_get(nop_ctx *ctx, float *params);
+
+/* Operator files.  A trained operator (its configuration and FP32
+ * parameters, Table A1's training result at p*) is kept in a binary file,
+ * all numbers little-endian whatever the host:
+ *   bytes  0..7   magic "NOPNET01"
+ *          8..35  int32 kind, sensors, width, basis, depth, modes, proj
+ *         36..59  float64 sigma_t_star, sigma_s_star, length
+ *         60..67  int64 n = nop_no_param_count(config)
+ *         68..    n float32 parameters in the order of nop_no_set.
+ * nop_no_write_file / nop_no_read_file are host-only (no context, no GPU).
+ * read: *n_inout holds the capacity of params (entries); on success it
+ * receives n and params the values; params may be NULL to query n (cfg is
+ * then still filled).  Errors: NOP_EINVAL (NULL path/cfg, invalid
+ * configuration, params too small), NOP_EIO (cannot open, short read or
+ * write, bad magic, n inconsistent with the configuration, trailing bytes).
+ * nop_no_save writes the context's current operator (NOP_ESTATE without
+ * one); nop_no_load reads a file and installs it as nop_no_set does. */
+int nop_no_write_file(const char *path, const nop_no_config *cfg, const float *params);
+int nop_no_read_file(const char *path, nop_no_config *cfg, float *params, long long *n_inout);
+int nop_no_save(nop_ctx *ctx, const char *path);
+int nop_no_load(nop_ctx *ctx, const char *path);
 
 /* Raw network forward on n samples (no scaling): DeepONet inputs [n][sensors],
  * coords [n_coords] (x/length), out [n][n_coords]; FNO inputs [n][grid points]

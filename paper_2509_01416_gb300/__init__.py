@@ -53,7 +53,31 @@ def unflatten_params(cfg, flat, like):
         o += n
     return out
 
-__all__ = ["Solver", "NopError", "capi"]
+def no_write_file(path, cfg, params):
+    """Write an operator file (format in include/nop.h); params: dict or flat FP32."""
+    flat = (np.ascontiguousarray(params, dtype=np.float32) if not isinstance(params, dict)
+            else flatten_params(cfg, params))
+    rc = capi.lib().nop_no_write_file(str(path).encode(), C.byref(cfg), capi._ptr(flat, capi._fp))
+    if rc != 0:
+        raise NopError(rc, "nop_no_write_file %s" % path)
+
+
+def no_read_file(path):
+    """Read an operator file: (nop_no_config, flat FP32 parameters)."""
+    cfg = capi.nop_no_config()
+    n = C.c_longlong(0)
+    L = capi.lib()
+    rc = L.nop_no_read_file(str(path).encode(), C.byref(cfg), None, C.byref(n))
+    if rc == 0:
+        flat = np.zeros(n.value, dtype=np.float32)
+        rc = L.nop_no_read_file(str(path).encode(), C.byref(cfg), capi._ptr(flat, capi._fp),
+                                C.byref(n))
+    if rc != 0:
+        raise NopError(rc, "nop_no_read_file %s" % path)
+    return cfg, flat
+
+
+__all__ = ["Solver", "NopError", "capi", "no_write_file", "no_read_file"]
 
 
 def _opts(tol=1e-6, itmax=10000, precision=NOP_PREC_F32, tol_k=1e-7, tol_inner=None,
@@ -131,6 +155,16 @@ class Solver:
         self._check(self._L.nop_no_set(self.h, C.byref(cfg), capi._ptr(flat, capi._fp)),
                     "nop_no_set")
         self.no_cfg, self.no_like = cfg, {k: np.asarray(v) for k, v in params.items()}
+
+    def no_save(self, path):
+        self._check(self._L.nop_no_save(self.h, str(path).encode()), "nop_no_save")
+
+    def no_load(self, path, like=None):
+        """Install the operator of a file; like: optional dict of arrays whose
+        shapes no_get() then uses."""
+        self._check(self._L.nop_no_load(self.h, str(path).encode()), "nop_no_load")
+        self.no_cfg, _ = no_read_file(path)
+        self.no_like = like
 
     def no_get(self):
         n = C.c_longlong()

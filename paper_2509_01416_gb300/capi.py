@@ -13,7 +13,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libnop.so")
 
 NOP_OK, NOP_EINVAL, NOP_ECUDA, NOP_ENOMEM = 0, -1, -2, -3
-NOP_ENOCONV, NOP_EDIVERGE, NOP_ETIMEOUT, NOP_ENAN, NOP_ESTATE = -4, -5, -6, -7, -8
+NOP_ENOCONV, NOP_EDIVERGE, NOP_ETIMEOUT, NOP_ENAN, NOP_ESTATE, NOP_EIO = -4, -5, -6, -7, -8, -9
 NOP_GEOM_SLAB, NOP_GEOM_XY = 1, 2
 NOP_BC_VACUUM, NOP_BC_REFLECTIVE = 0, 1
 NOP_PREC_F32, NOP_PREC_F64 = 0, 1
@@ -94,6 +94,11 @@ SIGNATURES = {
     "nop_no_param_count": (C.c_int, [C.POINTER(nop_no_config), C.POINTER(C.c_longlong)]),
     "nop_no_set": (C.c_int, [C.c_void_p, C.POINTER(nop_no_config), _fp]),
     "nop_no_get": (C.c_int, [C.c_void_p, _fp]),
+    "nop_no_write_file": (C.c_int, [C.c_char_p, C.POINTER(nop_no_config), _fp]),
+    "nop_no_read_file": (C.c_int, [C.c_char_p, C.POINTER(nop_no_config), _fp,
+                                   C.POINTER(C.c_longlong)]),
+    "nop_no_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "nop_no_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "nop_no_forward": (C.c_int, [C.c_void_p, C.c_int, _fp, _fp, C.c_int, _fp]),
     "nop_no_loss_grad": (C.c_int, [C.c_void_p, C.c_int, _fp, _fp, C.c_int, _fp,
                                    C.POINTER(C.c_double), _fp]),

@@ -131,6 +131,7 @@ const char* nop_status_str(int s) {
         case NOP_ETIMEOUT: return "device wait limit reached";
         case NOP_ENAN: return "non-finite value";
         case NOP_ESTATE: return "call out of order";
+        case NOP_EIO: return "file input/output failed";
         default: return "unknown status";
     }
 }

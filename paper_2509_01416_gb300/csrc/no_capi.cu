@@ -1,7 +1,10 @@
 // C ABI of the neural operator: install/read parameters, raw forward, loss
 // gradient, Adam training, input map, operator application, recast iteration.
 #include <algorithm>
+#include <cstdint>
+#include <cstdio>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include "nn_kernels.cuh"
@@ -101,6 +104,24 @@ __global__ void gather_rows_kernel(int nb, int w, const int* idx, const float* s
     dst[e] = src[(long long)idx[r] * w + c];
 }
 
+// operator files: little-endian byte encoding, independent of the host
+constexpr char NO_FILE_MAGIC[9] = "NOPNET01";
+constexpr size_t NO_FILE_HEAD = 68;
+
+void put_bytes(std::vector<unsigned char>& b, const char* p, size_t n) {
+    b.insert(b.end(), (const unsigned char*)p, (const unsigned char*)p + n);
+}
+
+void put_le(std::vector<unsigned char>& b, uint64_t v, int nbytes) {
+    for (int k = 0; k < nbytes; ++k) b.push_back((unsigned char)((v >> (8 * k)) & 0xffu));
+}
+
+uint64_t get_le(const unsigned char* p, int nbytes) {
+    uint64_t v = 0;
+    for (int k = 0; k < nbytes; ++k) v |= (uint64_t)p[k] << (8 * k);
+    return v;
+}
+
 }  // namespace
 
 extern "C" {
@@ -149,6 +170,110 @@ int nop_no_get(nop_ctx* ctx, float* params) {
                                       cudaMemcpyDeviceToHost, ctx->stream));
     NOP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     return NOP_OK;
+}
+
+int nop_no_write_file(const char* path, const nop_no_config* cfg, const float* params) {
+    if (!path || !cfg || !params) return NOP_EINVAL;
+    long long n;
+    if (nop_no_param_count(cfg, &n) != NOP_OK) return NOP_EINVAL;
+    std::vector<unsigned char> head;
+    put_bytes(head, NO_FILE_MAGIC, 8);
+    const int ints[7] = {cfg->kind, cfg->sensors, cfg->width, cfg->basis,
+                         cfg->depth, cfg->modes, cfg->proj};
+    for (int v : ints) put_le(head, (uint64_t)(uint32_t)v, 4);
+    for (double v : {cfg->sigma_t_star, cfg->sigma_s_star, cfg->length}) {
+        uint64_t u;
+        std::memcpy(&u, &v, 8);
+        put_le(head, u, 8);
+    }
+    put_le(head, (uint64_t)n, 8);
+    std::vector<unsigned char> body;
+    body.reserve((size_t)n * 4);
+    for (long long k = 0; k < n; ++k) {
+        uint32_t u;
+        std::memcpy(&u, &params[k], 4);
+        put_le(body, u, 4);
+    }
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return NOP_EIO;
+    const bool ok = std::fwrite(head.data(), 1, head.size(), f) == head.size() &&
+                    std::fwrite(body.data(), 1, body.size(), f) == body.size();
+    const bool closed = std::fclose(f) == 0;
+    return ok && closed ? NOP_OK : NOP_EIO;
+}
+
+int nop_no_read_file(const char* path, nop_no_config* cfg, float* params, long long* n_inout) {
+    if (!path || !cfg || !n_inout) return NOP_EINVAL;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return NOP_EIO;
+    std::vector<unsigned char> buf;
+    unsigned char tmp[65536];
+    size_t got;
+    while ((got = std::fread(tmp, 1, sizeof(tmp), f)) > 0) buf.insert(buf.end(), tmp, tmp + got);
+    const bool err = std::ferror(f) != 0;
+    std::fclose(f);
+    if (err || buf.size() < NO_FILE_HEAD || std::memcmp(buf.data(), NO_FILE_MAGIC, 8) != 0)
+        return NOP_EIO;
+    nop_no_config c{};
+    int* ints[7] = {&c.kind, &c.sensors, &c.width, &c.basis, &c.depth, &c.modes, &c.proj};
+    size_t at = 8;
+    for (int* v : ints) {
+        *v = (int)(uint32_t)get_le(buf.data() + at, 4);
+        at += 4;
+    }
+    for (double* v : {&c.sigma_t_star, &c.sigma_s_star, &c.length}) {
+        const uint64_t u = get_le(buf.data() + at, 8);
+        std::memcpy(v, &u, 8);
+        at += 8;
+    }
+    const long long n = (long long)get_le(buf.data() + at, 8);
+    at += 8;
+    long long want;
+    if (nop_no_param_count(&c, &want) != NOP_OK || n != want ||
+        buf.size() != NO_FILE_HEAD + (size_t)n * 4)
+        return NOP_EIO;
+    *cfg = c;
+    if (!params) {
+        *n_inout = n;
+        return NOP_OK;
+    }
+    if (*n_inout < n) return NOP_EINVAL;
+    for (long long k = 0; k < n; ++k) {
+        const uint32_t u = (uint32_t)get_le(buf.data() + at + 4 * k, 4);
+        std::memcpy(&params[k], &u, 4);
+    }
+    *n_inout = n;
+    return NOP_OK;
+}
+
+int nop_no_save(nop_ctx* ctx, const char* path) {
+    if (!ctx || !path) return NOP_EINVAL;
+    if (!ctx->no.loaded) {
+        ctx->set_error("no operator to save");
+        return NOP_ESTATE;
+    }
+    std::vector<float> p((size_t)ctx->no.n_params);
+    NOP_TRY(nop_no_get(ctx, p.data()));
+    const int rc = nop_no_write_file(path, &ctx->no.cfg, p.data());
+    if (rc != NOP_OK) ctx->set_error(std::string("cannot write operator file ") + path);
+    return rc;
+}
+
+int nop_no_load(nop_ctx* ctx, const char* path) {
+    if (!ctx || !path) return NOP_EINVAL;
+    nop_no_config c;
+    long long n = 0;
+    int rc = nop_no_read_file(path, &c, nullptr, &n);
+    std::vector<float> p;
+    if (rc == NOP_OK) {
+        p.resize((size_t)n);
+        rc = nop_no_read_file(path, &c, p.data(), &n);
+    }
+    if (rc != NOP_OK) {
+        ctx->set_error(std::string("cannot read operator file ") + path);
+        return rc;
+    }
+    return nop_no_set(ctx, &c, p.data());
 }
 
 int nop_no_forward(nop_ctx* ctx, int n, const float* inputs, const float* coords, int n_coords,
