@@ -23,6 +23,12 @@
 //              the group's own flux), phi}
 //   U[g][c] = {s (emission density used this iteration), phi_minus}
 // Norms, eigenvalue ratios and convergence tests are FP64 in every precision.
+//
+// Optionally (NOP_DSA) each group's sweep is followed by a diffusion synthetic
+// correction, a classical accelerator of the iteration kept for comparison
+// with the warm start: sn1d_dsa_factor factors every instance's edge
+// diffusion system once per solve, and dsa_pass solves it after each sweep on
+// one warp.
 #include <algorithm>
 #include <cmath>
 #include <numeric>
