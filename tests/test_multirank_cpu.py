@@ -59,3 +59,26 @@ def test_rank_batches_are_prefix_stable():
     for x, y in zip(a, b):
         assert x.I == y.I and x.N == y.N
         assert np.array_equal(x.sigt, y.sigt) and np.array_equal(x.Q, y.Q)
+
+
+@pytest.mark.timeout(300)
+def test_oracle_sample_leaves_no_work_queued():
+    # a timed oracle sample must not leave jobs in the pool for the next one
+    import multiprocessing as mp
+    import time
+    import bench
+    import workloads as W
+    insts = [W.slab_instance(np.random.default_rng(b), 200, 16) for b in range(600)]
+    pool = mp.get_context("spawn").Pool(2)
+    try:
+        bench.oracle_rate(insts[:4], 5.0, pool=pool)       # start the workers
+        # a short sample over the whole list (many seconds of work)...
+        bench.oracle_rate(insts, 0.05, seed=1, pool=pool)
+        # ...must not delay the next sample: it solves instances at once
+        t0 = time.perf_counter()
+        _, _, n2, el = bench.oracle_rate(insts, 1.0, seed=2, pool=pool)
+        assert n2 > 0 and el < 1.0 + 5.0
+        assert time.perf_counter() - t0 < 10.0
+    finally:
+        pool.terminate()
+        pool.join()
