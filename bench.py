@@ -117,21 +117,33 @@ def oracle_rate(insts, seconds, seed=0, pool=None):
 
 # ---------------------------------------------------------------- clocks
 class Clocks:
+    """nvidia-smi sampler (every 50 ms).  It starts before the plain-guess
+    runs, so it is sampling by the time the warm-start region is timed;
+    mark() brackets that region and summary() keeps the samples inside it
+    (all samples if their timestamps cannot be read)."""
+
     def __init__(self, idx, path):
         self.idx, self.path, self.p = idx, path, None
+        self.t0 = self.t1 = None
 
     def __enter__(self):
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + q,
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
         return self
+
+    def mark(self, start):
+        if start:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
 
     def __exit__(self, *a):
         if self.p:
@@ -143,23 +155,38 @@ class Clocks:
             self.f.close()
 
     def summary(self):
+        import datetime
         try:
-            rows = [r.split(",") for r in open(self.path).read().strip().splitlines()]
+            rows = [[c.strip() for c in r.split(",")]
+                    for r in open(self.path).read().strip().splitlines()]
         except Exception:
             return None
+        rows = [r for r in rows if len(r) > 9]
         if not rows:
             return None
-        sm = [float(r[1]) for r in rows if len(r) > 8]
-        mx = [float(r[2]) for r in rows if len(r) > 8]
+        inside = []
+        if self.t0 is not None and self.t1 is not None:
+            for r in rows:
+                try:
+                    ts = datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    inside = []
+                    break
+                if self.t0 - 0.05 <= ts <= self.t1 + 0.05:
+                    inside.append(r)
+        used = inside or rows
+        sm = [float(r[2]) for r in used]
+        mx = [float(r[3]) for r in used]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = set()
-        for r in rows:
-            for k, v in zip(names, r[5:9]):
-                if v.strip().lower() in ("active", "0x1", "1"):
+        for r in used:
+            for k, v in zip(names, r[6:10]):
+                if v.lower() in ("active", "0x1", "1"):
                     reasons.add(k)
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm),
+                "window": "timed warm-start region" if inside else "plain and warm-start runs"}
 
 
 # ------------------------------------------------------------------ main
@@ -255,7 +282,7 @@ def main():
         barrier()
         torch.cuda.synchronize()
         if clk:
-            clk.__enter__()
+            clk.mark(True)
             # the timed warm-start region is the one a profiler started with
             # --profile-from-start off records
             torch.cuda.profiler.start()
@@ -266,7 +293,7 @@ def main():
         torch.cuda.synchronize()
         if clk:
             torch.cuda.profiler.stop()
-            clk.__exit__()
+            clk.mark(False)
         barrier()
         tm = s.timing()
         s.set_timing(False)
@@ -274,8 +301,10 @@ def main():
 
     os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
     clk = Clocks(local, os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % rank))
+    clk.__enter__()
     plain_ms, plain_tm, plain_info = timed(False, max(1, args.steps // 2))
     ms_max, tm, info = timed(True, args.steps, clk)
+    clk.__exit__()
     value = whole_job_rate(world, B, args.steps, ms_max / 1e3)
     plain_value = whole_job_rate(world, B, max(1, args.steps // 2), plain_ms / 1e3)
     # the classical accelerator of the iteration itself on the same batch, alone

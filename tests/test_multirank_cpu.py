@@ -82,3 +82,28 @@ def test_oracle_sample_leaves_no_work_queued():
     finally:
         pool.terminate()
         pool.join()
+
+
+def test_clock_summary_keeps_the_timed_window(tmp_path):
+    import datetime
+    import bench
+    base = datetime.datetime(2026, 1, 2, 3, 4, 5)
+    rows = []
+    for k, (mhz, slow) in enumerate([(1200, "Not Active"), (2070, "Not Active"),
+                                     (2055, "Active"), (2070, "Not Active"), (990, "Not Active")]):
+        ts = (base + datetime.timedelta(milliseconds=100 * k)).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        rows.append("%s, 0, %d, 2070, 900.00, 0x0000000000000000, Not Active, Not Active, "
+                    "%s, Not Active" % (ts, mhz, slow))
+    f = tmp_path / "clocks.csv"
+    f.write_text("\n".join(rows) + "\n")
+    c = bench.Clocks(0, str(f))
+    c.t0 = (base + datetime.timedelta(milliseconds=100)).timestamp()
+    c.t1 = (base + datetime.timedelta(milliseconds=300)).timestamp()
+    s = c.summary()
+    assert s["samples"] == 3 and s["window"] == "timed warm-start region"
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_thermal_slowdown"]
+    # without a window every sample counts
+    c.t0 = c.t1 = None
+    s = c.summary()
+    assert s["samples"] == 5 and s["sm_mhz"] == 2055.0
