@@ -15,7 +15,6 @@ Prints one JSON line (rank 0).  Under torchrun each rank solves its own batch
 import argparse
 import collections
 import json
-import math
 import multiprocessing as mp
 import os
 import subprocess
@@ -236,7 +235,7 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
-    from paper_2509_01416_gb300 import Solver, capi
+    from paper_2509_01416_gb300 import Solver
     from tests.helpers import slab_batch_arrays
 
     n, wdt, order, sigt, sigs, src, _ = slab_batch_arrays(insts)
