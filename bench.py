@@ -19,6 +19,7 @@ import multiprocessing as mp
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -298,8 +299,8 @@ def main():
         s.set_timing(False)
         return max_over_ranks(ev0.elapsed_time(ev1), world, "cuda"), tm, info
 
-    os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-    clk = Clocks(local, os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % rank))
+    clk = Clocks(local, os.path.join(tempfile.gettempdir(),
+                                     "nop_bench_clocks_%d_rank%d.csv" % (os.getpid(), rank)))
     clk.__enter__()
     plain_ms, plain_tm, plain_info = timed(False, max(1, args.steps // 2))
     ms_max, tm, info = timed(True, args.steps, clk)
