@@ -161,7 +161,14 @@ class Clocks:
                     for r in open(self.path).read().strip().splitlines()]
         except Exception:
             return None
-        rows = [r for r in rows if len(r) > 9]
+        def numeric(r):
+            try:
+                float(r[2])
+                float(r[3])
+                return True
+            except ValueError:
+                return False
+        rows = [r for r in rows if len(r) > 9 and numeric(r)]
         if not rows:
             return None
         inside = []
