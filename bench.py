@@ -19,7 +19,6 @@ import multiprocessing as mp
 import os
 import subprocess
 import sys
-import tempfile
 import time
 
 import numpy as np
@@ -306,8 +305,7 @@ def main():
         s.set_timing(False)
         return max_over_ranks(ev0.elapsed_time(ev1), world, "cuda"), tm, info
 
-    clk = Clocks(local, os.path.join(tempfile.gettempdir(),
-                                     "nop_bench_clocks_%d_rank%d.csv" % (os.getpid(), rank)))
+    clk = Clocks(local, os.path.join(ROOT, ".bench_clocks_rank%d.csv" % rank))
     clk.__enter__()
     plain_ms, plain_tm, plain_info = timed(False, max(1, args.steps // 2))
     ms_max, tm, info = timed(True, args.steps, clk)
