@@ -212,20 +212,20 @@ def spectral2d_forward(v, R1r, R1i, R2r, R2i, quant=_id):
     B, ny, nx, C = v.shape
     m1, m2 = R1r.shape[:2]
     Fy, Fx, Ey, Ex = dft_mats_2d(ny, nx, m1, m2)
-    Vh = np.einsum("ky,lx,byxc->bklc", Fy, Fx, quant(v))      # (B, 2m1, m2, C)
+    Vh = np.einsum("ky,lx,byxc->bklc", Fy, Fx, quant(v), optimize=True)      # (B, 2m1, m2, C)
     Vq = quant(Vh.real) + 1j * quant(Vh.imag)
     R = np.concatenate([quant(R1r) + 1j * quant(R1i), quant(R2r) + 1j * quant(R2i)], axis=0)
     Wh = np.einsum("bklc,klco->bklo", Vq, R)
-    u = np.einsum("yk,xl,bklo->byxo", Ey, Ex, Wh).real
+    u = np.einsum("yk,xl,bklo->byxo", Ey, Ex, Wh, optimize=True).real
     return u, (Vq, R, Fy, Fx, Ey, Ex, m1)
 
 
 def spectral2d_backward(cache, du, quant=_id):
     Vq, R, Fy, Fx, Ey, Ex, m1 = cache
-    gW = np.einsum("yk,xl,byxo->bklo", np.conj(Ey), np.conj(Ex), du)
+    gW = np.einsum("yk,xl,byxo->bklo", np.conj(Ey), np.conj(Ex), du, optimize=True)
     gR = np.einsum("bklc,bklo->klco", np.conj(Vq), gW)
     gV = np.einsum("bklo,klco->bklc", gW, np.conj(R))
-    dv = np.einsum("ky,lx,bklc->byxc", np.conj(Fy), np.conj(Fx), gV).real
+    dv = np.einsum("ky,lx,bklc->byxc", np.conj(Fy), np.conj(Fx), gV, optimize=True).real
     return dv, (gR[:m1].real, gR[:m1].imag, gR[m1:].real, gR[m1:].imag)
 
 

@@ -169,13 +169,23 @@ def _measured_rate_bc(h, c, I, N, bcl, bcr, its=22, seed=0):
     return norms[-1] / norms[-2]
 
 
-def test_reflective_faces_and_the_lagged_right_face():
-    # the left face is read in the same iteration (mu > 0 sweeps after mu < 0):
-    # the unbounded-medium rate holds; the right face enters with the previous
-    # iteration's outflow, an error the P1 correction does not represent, and
-    # the rate settles near 0.31 c (still far below source iteration's c)
+def test_reflective_left_face_keeps_the_fourier_rate():
+    # the left face is read in the same iteration (mu > 0 sweeps after mu < 0),
+    # so the unbounded-medium Fourier rate holds (a physics-fixed value)
     c = 0.9
     left = _measured_rate_bc(0.1, c, 400, 16, T.REFLECTIVE, T.VACUUM)
-    right = _measured_rate_bc(0.1, c, 400, 16, T.VACUUM, T.REFLECTIVE)
     assert left == pytest.approx(_fourier_rate(16, c), rel=0.03)
+
+
+def test_lagged_right_face_rate_regression_pin():
+    """REGRESSION PIN, not a physics pin (parity unpinned): the right face
+    enters with the previous iteration's outflow, an error the P1 correction
+    does not represent.  Nothing derives the resulting rate; the window
+    0.28c-0.34c records what this oracle measured (about 0.31c), so the test
+    only detects a change of behaviour.  The physics-fixed bounds it must
+    also respect: slower than the unbounded-medium Fourier rate is allowed,
+    but it must stay well below plain source iteration's rate c."""
+    c = 0.9
+    right = _measured_rate_bc(0.1, c, 400, 16, T.VACUUM, T.REFLECTIVE)
+    assert right < c
     assert 0.28 * c < right < 0.34 * c

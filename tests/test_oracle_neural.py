@@ -147,6 +147,31 @@ def test_adam_first_step_closed_form():
     assert np.allclose(P["w"], w0 - 1e-3 * g["w"] / (np.abs(g["w"]) + 1e-8), atol=1e-15)
 
 
+def test_adam_second_step_closed_form():
+    """Two steps written out by hand for scalars (Kingma & Ba): with zero
+    initial moments, m_hat_2 = (b1 g1 + g2)/(1 + b1) and v_hat_2 =
+    (b2 g1^2 + g2^2)/(1 + b2); a wrong beta2, a missing bias correction or a
+    bias exponent off by one moves the second step."""
+    b1, b2, lr, eps = 0.9, 0.999, 1e-3, 1e-8
+    g1 = np.array([0.3, -2.0, 1e-3, 5.0])
+    g2 = np.array([-0.5, -1.0, 4e-3, 5.0])
+    P = {"w": np.array([1.0, -0.25, 0.0, 3.0])}
+    w0 = P["w"].copy()
+    m, v = {"w": np.zeros(4)}, {"w": np.zeros(4)}
+    NN.adam_step(P, {"w": g1}, m, v, 1, lr=lr, b1=b1, b2=b2, eps=eps)
+    NN.adam_step(P, {"w": g2}, m, v, 2, lr=lr, b1=b1, b2=b2, eps=eps)
+    step1 = g1 / (np.abs(g1) + eps)
+    mh = (b1 * g1 + g2) / (1 + b1)
+    vh = (b2 * g1 * g1 + g2 * g2) / (1 + b2)
+    expect = w0 - lr * step1 - lr * mh / (np.sqrt(vh) + eps)
+    assert np.allclose(P["w"], expect, rtol=0, atol=1e-15)
+    # first entry by hand: step 1 is 0.3/(0.3 + eps), then m_hat = -0.23/1.9,
+    # v_hat = 0.33991/1.999
+    by_hand = (1.0 - 1e-3 * 0.3 / (0.3 + eps)
+               - 1e-3 * (-0.23 / 1.9) / (np.sqrt(0.33991 / 1.999) + eps))
+    assert abs(P["w"][0] - by_hand) < 1e-13
+
+
 def test_mse_gradient():
     rng = np.random.default_rng(12)
     a, b = rng.standard_normal((3, 4)), rng.standard_normal((3, 4))
