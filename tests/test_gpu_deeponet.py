@@ -86,6 +86,31 @@ def test_adam_step_on_device(solver):
         assert np.max(np.abs(p1[k] - expect)) < 2e-6, k
 
 
+def test_three_adam_steps_match_oracle(solver):
+    """Three consecutive Adam steps (the moments and the step count persist
+    across nop_no_train calls) against oracle.neural.adam_step fed with the
+    device's own gradient of each step, moments carried in FP64."""
+    cfg, P = _small(solver, seed=8)
+    rng = np.random.default_rng(9)
+    U = rng.standard_normal((16, 32))
+    X = rng.uniform(0, 1, 9)
+    Y = rng.standard_normal((16, 9))
+    p = solver.no_get()
+    m = {k: np.zeros_like(v) for k, v in p.items()}
+    v2 = {k: np.zeros_like(v) for k, v in p.items()}
+    for t in (1, 2, 3):
+        _, g = solver.no_loss_grad(U, Y, X)
+        g = {k: a.astype(np.float32).astype(np.float64) for k, a in g.items()}
+        expect = {k: a.copy() for k, a in p.items()}
+        NN.adam_step(expect, g, m, v2, t, lr=1e-3)
+        solver.no_train(U, Y, X, steps=1, batch=16, lr=1e-3, order=np.arange(16))
+        p = solver.no_get()
+        for k in p:
+            assert np.max(np.abs(p[k] - expect[k])) < 2e-6, (t, k)
+        # continue from the device's parameters (FP32) so the steps stay comparable
+        p = {k: a.astype(np.float64) for k, a in p.items()}
+
+
 def test_input_map_matches_oracle_projection(solver):
     rng = np.random.default_rng(7)
     insts = [W.slab_instance(np.random.default_rng(b), I, 8) for b, I in
@@ -122,6 +147,27 @@ def test_predict_matches_oracle(solver, width, p):
         beta = op.coef((R.projection_matrix(edges, 128, 10.0) @ src)[None])
         ref = op.eval(beta, (np.arange(s.I) + 0.5) / s.I)[0]
         assert rel_l2(g, ref) < 5e-3
+
+
+def test_tensor_core_wait_limit_reports_timeout_and_recovers(solver):
+    """Failure detection without a fault: with the completion-wait bound at 0
+    the fused trunk kernel gives up at its first wait, lets the committed
+    products finish, frees its tensor memory and returns; the call reports
+    NOP_ETIMEOUT, and the same context then reproduces the normal result."""
+    from paper_2509_01416_gb300 import NopError, capi
+    insts = _setup_instances(solver, [100, 256, 77])
+    _small(solver, m=128, width=128, p=128, seed=9)
+    rng = np.random.default_rng(8)
+    src = np.concatenate([rng.uniform(-0.5, 1.0, s.I) for s in insts])
+    good = solver.no_predict(src)
+    solver.set_wait_limit(0)
+    try:
+        with pytest.raises(NopError) as e:
+            solver.no_predict(src)
+        assert e.value.code == capi.NOP_ETIMEOUT
+    finally:
+        solver.set_wait_limit(-1)
+    assert np.array_equal(solver.no_predict(src), good)
 
 
 @pytest.mark.parametrize("width,p", [(64, 32), (128, 128)])

@@ -144,6 +144,60 @@ def test_fno2d_gradients_match_oracle(solver):
     _check_grads(g, g0, gf)
 
 
+def test_fno1d_config_shape_forward_and_gradients(solver):
+    """The eigen-slab operator's own shape: FNO-1D width 64, 32 modes,
+    projection 128, on the 1000-cell grid, batch 2 (full tiles of every
+    transform and pointwise GEMM, plus a ragged tail of 1000 = 15 x 64 + 40)."""
+    n = 1000
+    cfg, P = _fno1(solver, 31, width=64, modes=32, proj=128)
+    rng = np.random.default_rng(32)
+    S = W.training_sources(33, 2, n) * 10.0
+    Y = rng.standard_normal((2, n))
+    xc = (np.arange(n) + 0.5) / n
+    got = solver.no_forward(S, coords=np.zeros(n))
+    q, _ = NN.fno1d_forward(P, S, xc, quant=NN.bf16_round)
+    f, _ = NN.fno1d_forward(P, S, xc)
+    # four 64-wide layers: the oracle's own BF16-vs-FP64 gap (sens) is near
+    # 1e-2 here, and the kernels add a second rounding pattern of that size
+    sens = rel_l2(q, f)
+    assert rel_l2(got, q) < max(1e-2, 3 * sens), sens
+    assert rel_l2(got, f) < max(3e-2, 4 * sens), sens
+    loss, g = solver.no_loss_grad(S, Y, coords=np.zeros(n))
+    out, cache = NN.fno1d_forward(P, S, xc, quant=NN.bf16_round)
+    l0, dout = NN.mse(out, Y)
+    g0 = NN.fno1d_backward(P, cache, dout, quant=NN.bf16_round)
+    of, cf = NN.fno1d_forward(P, S, xc)
+    gf = NN.fno1d_backward(P, cf, NN.mse(of, Y)[1])
+    assert abs(loss - l0) < 1e-2 * l0
+    _check_grads(g, g0, gf)
+
+
+def test_fno2d_config_shape_forward_and_gradients(solver):
+    """The x-y operator's own shape: FNO-2D width 32, 16 x 16 modes (two
+    weight blocks), projection 128, on the 256 x 256 mesh, batch 1."""
+    n = 256
+    _xy(solver, n, n, seed=34)
+    cfg, P = _fno2(solver, 35, width=32, modes=16, proj=128)
+    rng = np.random.default_rng(36)
+    S = W.training_sources_2d(37, 1, n) * 100.0
+    Y = rng.standard_normal((1, n, n))
+    c = (np.arange(n) + 0.5) / n
+    got = solver.no_forward(S.reshape(1, -1)).reshape(1, n, n)
+    q, _ = NN.fno2d_forward(P, S, c, c, quant=NN.bf16_round)
+    f, _ = NN.fno2d_forward(P, S, c, c)
+    sens = rel_l2(q, f)
+    assert rel_l2(got, q) < max(1e-2, 3 * sens), sens
+    assert rel_l2(got, f) < max(3e-2, 4 * sens), sens
+    loss, g = solver.no_loss_grad(S.reshape(1, -1), Y.reshape(1, -1))
+    out, cache = NN.fno2d_forward(P, S, c, c, quant=NN.bf16_round)
+    l0, dout = NN.mse(out, Y)
+    g0 = NN.fno2d_backward(P, cache, dout, quant=NN.bf16_round)
+    of, cf = NN.fno2d_forward(P, S, c, c)
+    gf = NN.fno2d_backward(P, cf, NN.mse(of, Y)[1])
+    assert abs(loss - l0) < 1e-2 * l0
+    _check_grads(g, g0, gf)
+
+
 def test_fno1d_training_lowers_the_loss(solver):
     n = 64
     cfg, P = _fno1(solver, 9, width=16, modes=8)

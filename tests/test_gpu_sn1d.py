@@ -13,7 +13,7 @@ import pytest
 import workloads as W
 from oracle import quadrature as Qd
 from oracle import transport as T
-from tests.helpers import oracle_slab, rel_l2, slab_batch_arrays, split
+from tests.helpers import eigen_slab_config3, oracle_slab, rel_l2, slab_batch_arrays, split
 
 pytestmark = pytest.mark.gpu
 
@@ -69,7 +69,7 @@ def test_heterogeneous_slab_fp32_within_workload_tolerance(solver):
 
 
 def test_three_region_eigen_fp32(solver):
-    c = W.eigen_slab_s32()
+    c = eigen_slab_config3()
     _set(solver, [c])
     quad = Qd.gauss_legendre(c.N)
     # same stopping rule on both sides (tol 1e-6 flux, 1e-7 in k, inner 1e-6)
@@ -80,7 +80,7 @@ def test_three_region_eigen_fp32(solver):
     assert rel_l2(phi, same.phi[0]) <= 1e-5
     # run to a tolerance whose truncation error is below the bar: converged oracle
     e = T.power_iteration(oracle_slab(c), quad, tol_k=1e-12, tol_phi=1e-10, tol_inner=1e-12)
-    assert 0.85 < e.k < 1.15
+    assert 0.9 <= e.k <= 1.1 and abs(e.k - c.k_target) < 1e-9
     k2, phi2, info2 = solver.solve_eigen(tol=1e-7, tol_k=1e-9, tol_inner=1e-7, itmax=5000,
                                          itmax_inner=2000, precision=0, check=False)
     assert abs(k2[0] - e.k) <= 1e-6, (k2[0], e.k, info2)

@@ -14,7 +14,7 @@ import workloads as W
 from oracle import neural as NN
 from oracle import recast as R
 from oracle import transport as T
-from tests.helpers import oracle_slab, rel_l2, slab_batch_arrays, split
+from tests.helpers import oracle_slab, rel_l2, slab_batch_arrays, split, xy_golden
 
 pytestmark = pytest.mark.gpu
 
@@ -256,7 +256,9 @@ def test_checkerboard_full_size_fno2d_warm_start(solver):
     assert np.all(np.isfinite(hist)) and hist[-10:].mean() < hist[:10].mean()
     solver.set_xy(c.nx, c.ny, c.Lx, c.Ly, c.sigt.reshape(-1), c.sigs.reshape(-1),
                   nu_sigma_f=c.nusigf.reshape(-1), chi=c.chi, bc=bc)
-    kw = dict(tol=1e-6, tol_k=1e-7, tol_inner=1e-6, itmax=2000, itmax_inner=500, check=False)
+    # stopping at a 2e-7 change keeps the truncation error below the bars
+    kw = dict(tol=2e-7, tol_k=1e-9, tol_inner=2e-7, itmax=2000, itmax_inner=400,
+              allow_noconv=True)
     kp, php, ip = solver.solve_eigen(**kw)
     t3 = time.perf_counter()
     kw_, phw, iw = solver.solve_eigen(warm_start=1, recast_tol=1e-2, recast_itmax=10, **kw)
@@ -266,5 +268,8 @@ def test_checkerboard_full_size_fno2d_warm_start(solver):
               t1 - t0, t2 - t1, t3 - t2, ip["outer"], t4 - t3, iw["outer"],
               iw["recast_iterations"], iw["recast_status"]))
     assert iw["recast_iterations"] > 0
-    assert abs(kw_[0] - kp[0]) < 1e-6, (kw_, kp, iw)
-    assert rel_l2(phw, php) < 1e-4
+    # both solves against the converged FP64 oracle (golden file), not each other
+    k0, g, j, i, ref, _ = xy_golden()
+    for kk, ph in ((kp, php), (kw_, phw)):
+        assert abs(kk[0] - k0) <= 1e-6, (kk[0], k0, ip, iw)
+        assert rel_l2(ph.reshape(c.sigt.shape)[g, j, i], ref) <= 1e-5

@@ -114,7 +114,11 @@ def eigen_slab_s32(seed=3):
     target = rng.uniform(0.9, 1.1)
     kinf = float(np.sum(shape)) / float(np.sum(sigt - sigs))
     nusigf = shape * target / (kinf * _bare_slab_nonleakage(sigt, sigs, L_SLAB))
-    return Slab1G(I=I, N=32, sigt=sigt, sigs=sigs, nusigf=nusigf)
+    inst = Slab1G(I=I, N=32, sigt=sigt, sigs=sigs, nusigf=nusigf)
+    # the eigenvalue this instance is meant to have; a caller that solved it
+    # once (eigenvalue lam) lands exactly there by scaling nusigf by target/lam
+    inst.k_target = float(target)
+    return inst
 
 
 @dataclass
@@ -240,6 +244,21 @@ def training_sources_2d(seed, n_samples, n, L=10.0, ell=1.2, var=3e-4, mean=0.07
     s = np.maximum(mean + f, 0.0)
     h = L / n
     return s / (s.sum(axis=(1, 2), keepdims=True) * h * h)
+
+
+def slab_batch_arrays(insts):
+    """Pack single-group slab instances into the flat arrays of the C ABI's
+    slab batch: (n_cells, width, order, sigma_t, sigma_s, source, nu_sigma_f),
+    cells of all instances concatenated in instance order (None for a field
+    the instances do not carry)."""
+    n = np.array([s.I for s in insts], dtype=np.int32)
+    wdt = np.array([s.L for s in insts])
+    order = np.array([s.N for s in insts], dtype=np.int32)
+    sigt = np.concatenate([s.sigt for s in insts])
+    sigs = np.concatenate([s.sigs for s in insts])
+    src = None if insts[0].Q is None else np.concatenate([s.Q for s in insts])
+    nsf = None if insts[0].nusigf is None else np.concatenate([s.nusigf for s in insts])
+    return n, wdt, order, sigt, sigs, src, nsf
 
 
 # ---------------------------------------------------------------------------
