@@ -243,9 +243,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     from paper_2509_01416_gb300 import Solver
-    from tests.helpers import slab_batch_arrays
-
-    n, wdt, order, sigt, sigs, src, _ = slab_batch_arrays(insts)
+    n, wdt, order, sigt, sigs, src, _ = W.slab_batch_arrays(insts)
     B, Ctot = len(insts), int(n.sum())
     stream = torch.cuda.Stream()
     s = Solver(local)

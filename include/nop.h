@@ -381,24 +381,30 @@ int nop_sp_eigen(nop_ctx *ctx, double tol, int itmax, int flags, double *phi_out
 
 /* Solve one single-group fixed-source slab (vacuum faces, zero initial flux,
  * FP32 sweeps with FP64 norms, Gauss-Legendre S_N) without allocating any
- * memory.  For callers that cannot call cudaMalloc -- code that runs while a
- * stream is captured into a graph, or hosts that forbid device allocations
- * outside a reserved budget.  The paper has no counterpart; this is a library
- * convenience.
+ * memory.  For callers that cannot call cudaMalloc: plug-ins whose host
+ * application owns the device memory and forbids allocations outside the
+ * budget it reserved, or real-time loops that must not touch the allocator
+ * (a cudaMalloc can take milliseconds and synchronise the device).  The
+ * paper has no counterpart; this is a library convenience.
  *
  * All pointers are device pointers: sigma_t, sigma_s (in-group scattering),
  * source (the isotropic S of Eq. 12) are [n_cells] doubles on equal cells
  * over [0, width]; phi_out receives the [n_cells] scalar flux; stats_out
- * receives {source iterations, status (0 or NOP_ENOCONV / NOP_ENAN)}.  Work
- * is enqueued on `stream` (a cudaStream_t, NULL = legacy default stream) and
- * the call returns without synchronising.
+ * receives {source iterations, status}: 0, NOP_ENOCONV (itmax reached; the
+ * flux is the last iterate), NOP_ENAN, or NOP_EINVAL when a coefficient is
+ * invalid (sigma_t not positive and finite, sigma_s or source not finite;
+ * found on the device, the flux is then zero).  Work is enqueued on `stream`
+ * (a cudaStream_t, NULL = legacy default stream) and the call returns
+ * without synchronising.
  *
  * Limits: n_cells <= NOP_NOALLOC_MAX_CELLS, even order <= NOP_NOALLOC_MAX_ORDER;
- * anything larger returns NOP_EINVAL.  The scratch is one fixed device array
- * of about 1.8 MB that every GPU loading the library holds until exit; calls
- * that overlap on the GPU race on it and must be serialised by the caller.
- * The first call on a device (with that device current) looks up the array's
- * address; make it before any stream capture. */
+ * anything larger returns NOP_EINVAL at once.  The scratch is one fixed
+ * device array of about 1.8 MB that every GPU loading the library holds
+ * until exit; every call shares it, so calls that overlap on the GPU race on
+ * it and must be serialised by the caller.  The first call on a device (with
+ * that device current) looks up the array's address and sets the solve
+ * kernel's shared-memory limit; make that first call before any stream
+ * capture. */
 int nop_slab_solve_noalloc(const double *sigma_t, const double *sigma_s,
                            const double *source, int n_cells, double width, int order,
                            double tol, int itmax, double *phi_out, int *stats_out,
@@ -423,6 +429,15 @@ typedef struct {
     double last_inst_mean_ms;/* last slab solve: mean instance duration          */
     int last_block_instances;/* last slab solve: instances run on a whole block  */
 } nop_timings;
+
+/* Failure detection.  Every wait of a tensor-core kernel on its own products
+ * (an mbarrier poll) is bounded; when the bound runs out the kernel records
+ * the failure, lets the products it committed finish, frees its tensor
+ * memory and returns, and the call reports NOP_ETIMEOUT with the context
+ * still usable.  polls < 0 restores the library default (2^26 polls, seconds
+ * of waiting); polls >= 0 sets the bound, 0 giving up at the first wait (a
+ * way to exercise the failure path).  Not in the paper: a library safeguard. */
+int nop_set_wait_limit(nop_ctx *ctx, long long polls);
 
 /* enable != 0: from now on record CUDA events around every kernel phase on
  * the context stream and count launches (totals reset); 0: stop recording.

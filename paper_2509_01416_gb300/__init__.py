@@ -128,6 +128,11 @@ class Solver:
     def set_stream(self, stream_handle):
         self._check(self._L.nop_set_stream(self.h, C.c_void_p(stream_handle)), "nop_set_stream")
 
+    def set_wait_limit(self, polls=-1):
+        """Bound of the tensor-core kernels' completion waits (nop_set_wait_limit);
+        -1 restores the default."""
+        self._check(self._L.nop_set_wait_limit(self.h, int(polls)), "nop_set_wait_limit")
+
     def set_timing(self, enable=True):
         self._check(self._L.nop_set_timing(self.h, 1 if enable else 0), "nop_set_timing")
 
@@ -307,9 +312,17 @@ class Solver:
         st.inst_iterations, st.inst_status = capi._ptr(it, capi._ip), capi._ptr(ss, capi._ip)
         return st, it, ss
 
-    def solve_fixed_source(self, phi0=None, check=True, out=None, **kw):
+    def _rc(self, rc, check, allow_noconv, what):
+        """Raise on a failed call.  NOP_ENOCONV (an iteration cap reached; the
+        outputs hold the last iterate) raises too unless allow_noconv."""
+        if check and rc != 0 and not (allow_noconv and rc == capi.NOP_ENOCONV):
+            self._check(rc, what)
+
+    def solve_fixed_source(self, phi0=None, check=True, out=None, allow_noconv=False, **kw):
         """Fixed-source solve; out: optional float64 host array of G*C entries
-        (for instance a pinned buffer) that receives the flux."""
+        (for instance a pinned buffer) that receives the flux.  Raises NopError
+        on any failure, including an instance that reached the iteration cap,
+        unless check=False or (for the cap alone) allow_noconv=True."""
         o = _opts(**kw)
         phi = self._out(out)
         p0 = None if phi0 is None else capi._f64(phi0)
@@ -317,26 +330,28 @@ class Solver:
         rc = self._L.nop_solve_fixed_source(self.h, C.byref(o),
                                             None if p0 is None else p0.ctypes.data,
                                             phi.ctypes.data, C.byref(st))
-        if check and rc not in (0, capi.NOP_ENOCONV):
-            self._check(rc, "nop_solve_fixed_source")
+        self._rc(rc, check, allow_noconv, "nop_solve_fixed_source")
         return phi, {"rc": rc, "iterations": it, "status": ss, "max_change": st.max_change,
                      "recast_iterations": st.recast_iterations,
                      "recast_status": st.recast_status}
 
-    def solve_fixed_source_dev(self, phi_out_ptr, phi0_ptr=None, **kw):
+    def solve_fixed_source_dev(self, phi_out_ptr, phi0_ptr=None, check=True, allow_noconv=False,
+                               **kw):
         """Device-resident variant: phi_out_ptr (and phi0_ptr) are device pointers
-        to FP64 arrays of G*C entries; per-instance statistics come back to the host."""
+        to FP64 arrays of G*C entries; per-instance statistics come back to the
+        host.  Failures raise as in solve_fixed_source."""
         flags = capi.NOP_OUT_DEVICE | (capi.NOP_PHI0_DEVICE if phi0_ptr else 0)
         o = _opts(flags=flags, **kw)
         st, it, ss = self._stats()
         rc = self._L.nop_solve_fixed_source(self.h, C.byref(o), phi0_ptr, phi_out_ptr,
                                             C.byref(st))
-        if rc not in (0, capi.NOP_ENOCONV):
-            self._check(rc, "nop_solve_fixed_source")
+        self._rc(rc, check, allow_noconv, "nop_solve_fixed_source")
         return {"rc": rc, "iterations": it, "status": ss,
                 "recast_iterations": st.recast_iterations, "recast_status": st.recast_status}
 
-    def solve_eigen(self, phi0=None, k0=0.0, check=True, out=None, **kw):
+    def solve_eigen(self, phi0=None, k0=0.0, check=True, out=None, allow_noconv=False, **kw):
+        """Eigen solve: (k per instance, phi, info).  Failures raise as in
+        solve_fixed_source (an outer iteration cap is NOP_ENOCONV)."""
         o = _opts(**kw)
         phi = self._out(out)
         k = np.zeros(self.n_inst)
@@ -344,8 +359,7 @@ class Solver:
         st, it, ss = self._stats()
         rc = self._L.nop_solve_eigen(self.h, C.byref(o), None if p0 is None else p0.ctypes.data,
                                      float(k0), phi.ctypes.data, k.ctypes.data, C.byref(st))
-        if check and rc not in (0, capi.NOP_ENOCONV):
-            self._check(rc, "nop_solve_eigen")
+        self._rc(rc, check, allow_noconv, "nop_solve_eigen")
         return k, phi, {"rc": rc, "inner": it, "status": ss, "outer": st.max_outer,
                         "max_change": st.max_change,
                         "recast_iterations": st.recast_iterations,

@@ -88,6 +88,7 @@ SIGNATURES = {
     "nop_solve_fixed_source": (C.c_int, [C.c_void_p, C.POINTER(nop_solve_opts), C.c_void_p,
                                          C.c_void_p, C.POINTER(nop_stats)]),
     "nop_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
+    "nop_set_wait_limit": (C.c_int, [C.c_void_p, C.c_longlong]),
     "nop_slab_solve_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                                          C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
                                          C.c_void_p]),

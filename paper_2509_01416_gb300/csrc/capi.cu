@@ -179,6 +179,12 @@ int nop_set_stream(nop_ctx* ctx, void* stream) {
     return NOP_OK;
 }
 
+int nop_set_wait_limit(nop_ctx* ctx, long long polls) {
+    if (!ctx) return NOP_EINVAL;
+    ctx->wait_limit = polls < 0 ? -1 : polls;
+    return NOP_OK;
+}
+
 int nop_set_timing(nop_ctx* ctx, int enable) {
     if (!ctx) return NOP_EINVAL;
     NOP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));

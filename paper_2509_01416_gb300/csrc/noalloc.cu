@@ -1,25 +1,30 @@
 // Allocation-free slab solve.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA stream is
-// being captured into a graph, plug-ins whose host process forbids device
-// allocations outside a pre-reserved budget, or real-time loops that must not
-// touch the allocator.  nop_slab_solve_noalloc serves them: it solves one
-// single-group fixed-source slab with the library's FP32 slab kernel, and
-// every intermediate buffer lives in the file-scope device array below.  The
-// array is a fixed cost of every GPU that loads the library and is held until
-// the process exits.
+// Some callers cannot call cudaMalloc: plug-ins whose host application owns
+// the device memory and forbids allocations outside a budget it reserved up
+// front, or real-time control loops that must not touch the allocator (a
+// cudaMalloc can take milliseconds and can synchronise the device).
+// nop_slab_solve_noalloc serves them: it solves one single-group
+// fixed-source slab with the library's FP32 slab kernel, and every
+// intermediate buffer lives in the file-scope device array below.  The array
+// is a fixed cost of every GPU that loads the library and is held until the
+// process exits.  The paper has no counterpart; this is a library convenience.
 //
 // The array is shared by every call: calls that overlap on the GPU (two
 // streams, or two host threads) race on it and must be serialised by the
-// caller.  A call clears what has to start at zero (work counters, boundary
-// fluxes) and overwrites everything else before reading it.
+// caller.  A call clears what has to start at zero (work counters, status)
+// and overwrites everything else before reading it; the solve kernel itself
+// clears the boundary fluxes.  The Gauss-Legendre set of the last order
+// solved on a device stays in the array and is rebuilt only when the order
+// changes.
 //
 // Set-up: the first call on a device, with that device current, looks up the
 // array's device address (cudaGetSymbolAddress) and raises the solve
-// kernel's shared-memory limit; later calls on that device reuse the cached
-// address.  The first call on each device should therefore come before any
-// stream capture.  In host code the array's name is only a host-side stand-in,
-// which is why the kernels receive the looked-up address.
+// kernel's dynamic shared-memory limit (cudaFuncSetAttribute); later calls on
+// that device reuse both.  In host code the array's name is only a host-side
+// stand-in, not a device address, which is why the kernels receive the
+// looked-up address.  The first call on each device should come before any
+// stream capture.
 #include <cmath>
 
 #include "sn1d_impl.cuh"
@@ -46,44 +51,14 @@ static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];
 
 constexpr int MAX_DEVICES = 64;
 unsigned char* g_addr[MAX_DEVICES] = {nullptr};
-
-// Gauss-Legendre nodes (ascending) and weights of order N by Newton on P_N.
-__global__ void gl_kernel(int N, double* mu, double* w) {
-    for (int n = threadIdx.x; n < N; n += blockDim.x) {
-        double x = -cos(M_PI * (n + 0.75) / (N + 0.5)), p0 = 1.0, p1 = x, dp = 1.0;
-        for (int it = 0; it < 100; ++it) {
-            p0 = 1.0;
-            p1 = x;
-            for (int k = 1; k < N; ++k) {
-                const double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
-                p0 = p1;
-                p1 = p2;
-            }
-            dp = N * (x * p1 - p0) / (x * x - 1.0);
-            const double dx = p1 / dp;
-            x -= dx;
-            if (fabs(dx) < 1e-16) break;
-        }
-        p0 = 1.0;
-        p1 = x;
-        for (int k = 1; k < N; ++k) {
-            const double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
-            p0 = p1;
-            p1 = p2;
-        }
-        dp = N * (x * p1 - p0) / (x * x - 1.0);
-        mu[n] = x;
-        w[n] = 2.0 / ((1.0 - x * x) * dp * dp);
-    }
-}
+int g_order[MAX_DEVICES] = {0};   // order of the quadrature held in the array
 
 // Instance table of the single instance; clears the work counters and the
-// boundary fluxes, which must start at zero.
+// outputs, which must start at zero.
 __global__ void init_kernel(unsigned char* base, int I, int N, double dx, int cfg) {
     int* ints = (int*)(base + OFF_INT);
     long long* ll = (long long*)(base + OFF_LL);
     double* dbl = (double*)(base + OFF_DBL);
-    float* psib = (float*)(base + OFF_PSIB);
     if (threadIdx.x == 0) {
         ints[0] = 0;      // order list: instance 0
         ints[1] = 0;      // small-queue counter
@@ -102,7 +77,23 @@ __global__ void init_kernel(unsigned char* base, int I, int N, double dx, int cf
         dbl[2] = 0.0;     // final change
         dbl[3] = 0.0;     // k out (unused)
     }
-    for (int e = threadIdx.x; e < N; e += blockDim.x) psib[e] = 0.f;
+}
+
+// The coefficient check of nop_set_problem, on the device and without a host
+// synchronisation: sigma_t must be positive and finite, sigma_s and the
+// source finite.  A bad instance gets status NOP_EINVAL and zero iterations,
+// and its work counter is taken, so the solve kernel that follows finds no
+// instance to run and leaves the flux at zero.
+__global__ void coef_check_kernel(unsigned char* base, int I, const double* sigt,
+                                  const double* sigs, const double* src) {
+    bool bad = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < I; i += gridDim.x * blockDim.x)
+        bad |= !(sigt[i] > 0.0) || !isfinite(sigt[i]) || !isfinite(sigs[i]) || !isfinite(src[i]);
+    if (bad) {
+        int* ints = (int*)(base + OFF_INT);
+        ints[1] = 1;             // the one instance is taken: the solve skips it
+        ints[8] = NOP_EINVAL;    // status out (same value from every writer)
+    }
 }
 
 __global__ void stats_kernel(const unsigned char* base, int* stats_out) {
@@ -117,7 +108,12 @@ namespace nop {
 int sn1d_launch_f32(const Sn1dArgs& a, long long C, const double* sigt, const double* sigs,
                     const double* src, Cell4<float>* X, float* ext, double* phi_out,
                     cudaStream_t stream);
-}
+int sn1d_f32_raise_smem_limit();
+// Gauss-Legendre nodes and weights of the orders listed in device memory
+// (csrc/quadrature.cu).
+__global__ void gauss_legendre_kernel(const int* orders, const int* offs, int n_orders,
+                                      double* mu, double* w);
+}  // namespace nop
 
 extern "C" int nop_slab_solve_noalloc(const double* sigma_t, const double* sigma_s,
                                       const double* source, int n_cells, double width, int order,
@@ -130,19 +126,33 @@ extern "C" int nop_slab_solve_noalloc(const double* sigma_t, const double* sigma
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return NOP_ECUDA;
     if (!g_addr[dev]) {
+        // once per device, with that device current
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return NOP_ECUDA;
+        if (nop::sn1d_f32_raise_smem_limit() != NOP_OK) return NOP_ECUDA;
         g_addr[dev] = (unsigned char*)p;
+        g_order[dev] = 0;
     }
     unsigned char* base = g_addr[dev];
     cudaStream_t st = (cudaStream_t)stream;
     int lg, A;
     nop::sn1d_pick_config(n_cells, order, &lg, &A);
     const double dx = width / n_cells;
-    gl_kernel<<<1, 128, 0, st>>>(order, (double*)(base + OFF_MU), (double*)(base + OFF_W));
-    init_kernel<<<1, 128, 0, st>>>(base, n_cells, order, dx, (lg << 8) | A);
-    if (cudaGetLastError() != cudaSuccess) return NOP_ECUDA;
     int* ints = (int*)(base + OFF_INT);
+    init_kernel<<<1, 32, 0, st>>>(base, n_cells, order, dx, (lg << 8) | A);
+    if (g_order[dev] != order) {
+        // ints[4] holds the order and ints[5] the offset 0 (written just above)
+        nop::gauss_legendre_kernel<<<1, 64, 0, st>>>(ints + 4, ints + 5, 1,
+                                                      (double*)(base + OFF_MU),
+                                                      (double*)(base + OFF_W));
+    }
+    coef_check_kernel<<<(n_cells + 255) / 256, 256, 0, st>>>(base, n_cells, sigma_t, sigma_s,
+                                                             source);
+    if (cudaGetLastError() != cudaSuccess) {
+        g_order[dev] = 0;
+        return NOP_ECUDA;
+    }
+    g_order[dev] = order;
     long long* ll = (long long*)(base + OFF_LL);
     double* dbl = (double*)(base + OFF_DBL);
     nop::Sn1dArgs a{};

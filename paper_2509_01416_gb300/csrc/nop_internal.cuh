@@ -102,6 +102,9 @@ struct nop_ctx {
     double *sigt_d = nullptr, *sigs_d = nullptr, *src_d = nullptr, *nsf_d = nullptr,
            *chi_d = nullptr, *sigs1_d = nullptr;
 
+    // mbarrier poll limit of the tensor-core kernels (nop_set_wait_limit);
+    // negative: the library default
+    long long wait_limit = -1;
     // phase timing (nop_set_timing)
     bool timing = false;
     struct Mark {

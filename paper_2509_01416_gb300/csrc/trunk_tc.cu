@@ -18,9 +18,11 @@
 // its row back with tcgen05.ld, adds the bias, applies ReLU, rounds to BF16
 // and stores the row as the next layer's A operand.  The inner products with
 // the coefficients are one more product (N = 32 instances per chunk).  Waits
-// are bounded: on a
-// timeout the kernel records an error, stops issuing work, frees its TMEM and
-// returns.
+// are bounded (TC_SPIN polls, or the context's nop_set_wait_limit): on a
+// timeout the kernel records an error and stops issuing work; a warpgroup
+// whose wait gave up then waits (bounded by TC_SPIN) for the products it
+// already committed, so no product still writes TMEM when the block frees it
+// and returns.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -88,9 +90,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t addr, uint32_t (&r)[32]) {
         : "r"(addr));
 }
 
-// waits for the phase of the mbarrier; false after the poll limit
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
-    for (long long it = 0; it < TC_SPIN; ++it) {
+// waits for the phase of the mbarrier; false after `limit` polls (none when
+// limit is 0)
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase, long long limit) {
+    for (long long it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -142,7 +145,7 @@ __global__ void __launch_bounds__(2 * TC_M, 1) trunk_tc_kernel(
     const int* grp_inst_off, const int* inst_list, const long long* cell_off, const float* W1,
     const float* b1, const float* W2, const float* b2, const float* W3, const float* b3,
     const float* W4, const float* b4, const float* beta_keep, const int* status, double* phi,
-    int* err) {
+    int* err, long long spin) {
     extern __shared__ unsigned char tc_raw[];
     // 1024-byte aligned operand area: W2-W4, then per warpgroup H and B
     __nv_bfloat16* base = (__nv_bfloat16*)(((uintptr_t)tc_raw + 1023) & ~(uintptr_t)1023);
@@ -195,6 +198,9 @@ __global__ void __launch_bounds__(2 * TC_M, 1) trunk_tc_kernel(
     const uint32_t h_addr = smem_addr(H);
     uint32_t phase = 0;
     int* abort_wg = &abort_flag[wg];
+    // the phase of a commit whose wait gave up (products possibly in flight)
+    bool stuck = false;
+    uint32_t stuck_phase = 0;
 
     for (long long t0 = ((long long)blockIdx.x * 2 + wg) * TC_M; t0 < P;
          t0 += (long long)gridDim.x * 2 * TC_M) {
@@ -249,12 +255,14 @@ __global__ void __launch_bounds__(2 * TC_M, 1) trunk_tc_kernel(
                     "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                         bar));
             }
-            const bool ok = mbar_wait(bar, phase);
-            phase ^= 1u;
+            const bool ok = mbar_wait(bar, phase, spin);
             if (!ok) {
                 atomicExch(err, 1);
                 *abort_wg = 1;
+                stuck = true;
+                stuck_phase = phase;
             }
+            phase ^= 1u;
             wg_sync(wg);
             if (*abort_wg) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
@@ -316,12 +324,14 @@ __global__ void __launch_bounds__(2 * TC_M, 1) trunk_tc_kernel(
                     "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                         bar));
             }
-            const bool ok = mbar_wait(bar, phase);
-            phase ^= 1u;
+            const bool ok = mbar_wait(bar, phase, spin);
             if (!ok) {
                 atomicExch(err, 1);
                 *abort_wg = 1;
+                stuck = true;
+                stuck_phase = phase;
             }
+            phase ^= 1u;
             wg_sync(wg);
             if (*abort_wg) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
@@ -341,6 +351,9 @@ __global__ void __launch_bounds__(2 * TC_M, 1) trunk_tc_kernel(
         }
         if (*abort_wg) break;
     }
+    // a wait that gave up left products in flight: let them finish (bounded)
+    // before the TMEM they write is freed
+    if (stuck) mbar_wait(bar, stuck_phase, TC_SPIN);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tslot));
@@ -361,7 +374,7 @@ int trunk_tc_launch(nop_ctx* ctx, long long P, const int4* tinfo, const long lon
         1, std::min<long long>((P + 2 * TC_M - 1) / (2 * TC_M), ctx->sm_count));
     trunk_tc_kernel<<<grid, 2 * TC_M, TC_SMEM, ctx->stream>>>(
         P, tinfo, gpt, gI, ginst, list, cell_off, W[0], b[0], W[1], b[1], W[2], b[2], W[3], b[3],
-        beta_keep, status, phi, err);
+        beta_keep, status, phi, err, ctx->wait_limit >= 0 ? ctx->wait_limit : TC_SPIN);
     NOP_CUDA_TRY(ctx, cudaGetLastError());
     ctx->count_launch(false);
     return NOP_OK;

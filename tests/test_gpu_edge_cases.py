@@ -79,7 +79,9 @@ def test_zero_source_gives_zero_flux(solver):
              W.slab_instance(np.random.default_rng(3), 80, 16)]
     _set(solver, insts)
     for prec in (0, 1):
-        phi, info = solver.solve_fixed_source(tol=1e-8, itmax=1000, precision=prec)
+        # FP32 need not reach a 1e-8 change: the cap (NOP_ENOCONV) is accepted there
+        phi, info = solver.solve_fixed_source(tol=1e-8, itmax=1000, precision=prec,
+                                              allow_noconv=prec == 0)
         z, other = split(phi, insts)
         assert np.all(z == 0.0) and info["status"][0] == 0
         assert rel_l2(other, _oracle(insts[1], 1e-8).phi[0]) < 1e-5
