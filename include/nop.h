@@ -85,9 +85,33 @@ extern "C" {
                               flux is unchanged.  NOP_EINVAL with sigma_s1 or
                               the x-y geometry.                               */
 
+#define NOP_SWEEP_CHUNKED 16 /* slabs: keep the chunked lane layout (angles x cell
+                              chunks with a warp scan of the chunk maps) even
+                              where the direct layout applies (vacuum faces,
+                              isotropic scattering, no NOP_DSA: the two
+                              direction halves swept at once, one lane per
+                              angle over the whole slab).  Same iteration,
+                              same answer up to rounding; a comparison and
+                              tuning aid.                                     */
+
+#define NOP_COLD_SCHEDULE 32 /* slabs: schedule without the iteration counts of
+                              earlier solves of the same batch layout (as for a
+                              batch seen for the first time); the answer is
+                              unchanged                                       */
+
+/* nop_solve_opts.schedule (slab batches).  NOP_SCHED_AUTO: each instance's
+ * lane layout (direct or chunked lanes) and whether it runs on one warp or on
+ * a 12-warp team come from costs measured on this device (the autotuner:
+ * buckets of instances not yet measured are timed once per context, a few
+ * milliseconds, on batches of NOP_SCHED_TUNE_MIN instances or more; smaller
+ * batches use the analytic model); NOP_SCHED_MODEL: the analytic cost model
+ * alone; NOP_SCHED_WARP / NOP_SCHED_BLOCK: every instance on one warp / on a
+ * team where its layout allows. */
 #define NOP_SCHED_AUTO   0
 #define NOP_SCHED_WARP   1
 #define NOP_SCHED_BLOCK  2
+#define NOP_SCHED_MODEL  3
+#define NOP_SCHED_TUNE_MIN 256
 
 typedef struct nop_ctx nop_ctx;
 
@@ -148,9 +172,10 @@ typedef struct {
     double recast_tol;     /* recast loop tolerance (Eq. 24)                   */
     int recast_itmax;      /* recast loop iteration cap                        */
     int flags;             /* NOP_PHI0_DEVICE | NOP_OUT_DEVICE | NOP_DSA       */
-    int schedule;          /* slab batches: NOP_SCHED_AUTO, NOP_SCHED_WARP (one
-                              warp per instance), NOP_SCHED_BLOCK (a whole block
-                              per instance where the angles allow it)         */
+    int schedule;          /* slab batches: NOP_SCHED_AUTO, NOP_SCHED_MODEL,
+                              NOP_SCHED_WARP (one warp per instance),
+                              NOP_SCHED_BLOCK (a whole block per instance
+                              where the layout allows it)                     */
 } nop_solve_opts;
 
 /* Per-call statistics (host struct).  Per-instance arrays are optional
@@ -428,7 +453,30 @@ typedef struct {
     double last_inst_max_ms; /* last slab solve: longest single instance         */
     double last_inst_mean_ms;/* last slab solve: mean instance duration          */
     int last_block_instances;/* last slab solve: instances run on a whole block  */
+    int last_direct_instances;/* last slab solve: instances on the direct lanes  */
+    double last_tune_ms;     /* last slab solve: host time spent measuring layout
+                                costs (0 when every bucket was known)          */
 } nop_timings;
+
+/* Measured arithmetic ceilings of the sweep (a microbenchmark, not the
+ * paper's method): the device's rate of the special-function reciprocal
+ * rcp.approx.ftz.f32 (one per diamond-difference cell-angle update) and of
+ * FP32 fused multiply-adds, in operations per second, from kernels of 8
+ * independent chains per thread over 8 blocks of 256 threads per SM, timed
+ * with CUDA events on the context stream (best of 3 after a warm-up).  Takes
+ * a few milliseconds. */
+int nop_measure_alu_peaks(nop_ctx *ctx, double *rcp_per_s, double *fma_per_s);
+
+/* The slab batch scheduler's team selection, exported so that its logic can
+ * be checked without a GPU (host arithmetic only).  lat_warp[b]: latency of
+ * instance b on one warp; lat_team[b]: on a team of team_width warps (< 0:
+ * no team).  mode 0: an instance gets a team when its warp latency exceeds
+ * the expected span S = (warp latencies of the warp instances + team_width x
+ * team latencies of the team instances) / warps, found by fixed-point rounds
+ * from the mean warp load; mode 1: every instance that can; mode 2: none.
+ * team_out[b] receives 0/1; *span_out (may be NULL) the final S. */
+int nop_sched_select_teams(int n, const double *lat_warp, const double *lat_team, int warps,
+                           int team_width, int mode, int *team_out, double *span_out);
 
 /* Failure detection.  Every wait of a tensor-core kernel on its own products
  * (an mbarrier poll) is bounded; when the bound runs out the kernel records

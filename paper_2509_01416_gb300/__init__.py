@@ -82,10 +82,14 @@ __all__ = ["Solver", "NopError", "capi", "no_write_file", "no_read_file"]
 
 def _opts(tol=1e-6, itmax=10000, precision=NOP_PREC_F32, tol_k=1e-7, tol_inner=None,
           itmax_inner=10000, warm_start=NOP_WARM_NONE, recast_tol=1e-4, recast_itmax=200,
-          flags=0, schedule=0, dsa=False):
+          flags=0, schedule=0, dsa=False, chunked=False, cold=False):
     o = capi.nop_solve_opts()
+    if cold:
+        flags |= capi.NOP_COLD_SCHEDULE
     if dsa:
         flags |= capi.NOP_DSA
+    if chunked:
+        flags |= capi.NOP_SWEEP_CHUNKED
     o.tol, o.tol_k = tol, tol_k
     o.tol_inner = tol if tol_inner is None else tol_inner
     o.itmax, o.itmax_inner, o.precision = itmax, itmax_inner, precision
@@ -132,6 +136,13 @@ class Solver:
         """Bound of the tensor-core kernels' completion waits (nop_set_wait_limit);
         -1 restores the default."""
         self._check(self._L.nop_set_wait_limit(self.h, int(polls)), "nop_set_wait_limit")
+
+    def measure_alu_peaks(self):
+        """(reciprocal/s, FP32 FMA/s) measured on this device (nop_measure_alu_peaks)."""
+        r, f = C.c_double(), C.c_double()
+        self._check(self._L.nop_measure_alu_peaks(self.h, C.byref(r), C.byref(f)),
+                    "nop_measure_alu_peaks")
+        return r.value, f.value
 
     def set_timing(self, enable=True):
         self._check(self._L.nop_set_timing(self.h, 1 if enable else 0), "nop_set_timing")

@@ -19,7 +19,10 @@ NOP_BC_VACUUM, NOP_BC_REFLECTIVE = 0, 1
 NOP_PREC_F32, NOP_PREC_F64 = 0, 1
 NOP_WARM_NONE, NOP_WARM_RECAST, NOP_WARM_RECAST_CP = 0, 1, 2
 NOP_PHI0_DEVICE, NOP_OUT_DEVICE, NOP_SP_CONSTRAINED, NOP_DSA = 1, 2, 4, 8
-NOP_SCHED_AUTO, NOP_SCHED_WARP, NOP_SCHED_BLOCK = 0, 1, 2
+NOP_SWEEP_CHUNKED = 16
+NOP_COLD_SCHEDULE = 32
+NOP_SCHED_AUTO, NOP_SCHED_WARP, NOP_SCHED_BLOCK, NOP_SCHED_MODEL = 0, 1, 2, 3
+NOP_SCHED_TUNE_MIN = 256
 NOP_NOALLOC_MAX_CELLS, NOP_NOALLOC_MAX_ORDER = 65536, 128
 
 _dp = C.POINTER(C.c_double)
@@ -55,7 +58,8 @@ class nop_timings(C.Structure):
                 ("setup_ms", C.c_double), ("launches", C.c_longlong),
                 ("sweep_launches", C.c_longlong), ("cell_angle_updates", C.c_double),
                 ("last_span_ms", C.c_double), ("last_inst_max_ms", C.c_double),
-                ("last_inst_mean_ms", C.c_double), ("last_block_instances", C.c_int)]
+                ("last_inst_mean_ms", C.c_double), ("last_block_instances", C.c_int),
+                ("last_direct_instances", C.c_int), ("last_tune_ms", C.c_double)]
 
 
 NOP_NO_DEEPONET, NOP_NO_FNO1D, NOP_NO_FNO2D = 1, 2, 3
@@ -89,6 +93,10 @@ SIGNATURES = {
                                          C.c_void_p, C.POINTER(nop_stats)]),
     "nop_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "nop_set_wait_limit": (C.c_int, [C.c_void_p, C.c_longlong]),
+    "nop_measure_alu_peaks": (C.c_int, [C.c_void_p, C.POINTER(C.c_double),
+                                        C.POINTER(C.c_double)]),
+    "nop_sched_select_teams": (C.c_int, [C.c_int, _dp, _dp, C.c_int, C.c_int, C.c_int, _ip,
+                                         C.POINTER(C.c_double)]),
     "nop_slab_solve_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                                          C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_void_p,
                                          C.c_void_p]),

@@ -532,7 +532,8 @@ int deeponet_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* sta
         it = imax + 1;   // skip the generic loop
     }
     int* active_h = nullptr;
-    NOP_CUDA_TRY(ctx, cudaMallocHost(&active_h, sizeof(int)));
+    NOP_TRY(ctx->pinned("rc_active", sizeof(int), &q));
+    active_h = (int*)q;
     for (it = it == 0 ? 1 : it; it <= imax; ++it) {
         split_kernel<<<B, 128, 0, ctx->stream>>>(M, h, PS, PD, u, Usp, sig, flags);
         if (cudaGetLastError() != cudaSuccess) { rc = NOP_ECUDA; break; }
@@ -573,7 +574,6 @@ int deeponet_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* sta
         }
         if (*active_h == 0) break;
     }
-    cudaFreeHost(active_h);
     if (rc != NOP_OK) {
         ctx->set_error("recast iteration failed");
         return rc;
@@ -581,41 +581,41 @@ int deeponet_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* sta
     // final flux at every cell centre
     const long long C = s.C;
     if (c.width == FT_W && c.basis == FT_W && c.depth == 4) {
-        // instances grouped by cell count (CSR): distinct points once
-        std::vector<int> order(B);
-        std::iota(order.begin(), order.end(), 0);
-        std::stable_sort(order.begin(), order.end(),
-                         [&](int x, int y) { return s.ncell[x] < s.ncell[y]; });
-        std::vector<long long> gpt(1, 0);
-        std::vector<int> gI, ginst(1, 0);
-        for (int k = 0; k < B; ++k) {
-            const int I = s.ncell[order[k]];
-            if (gI.empty() || gI.back() != I) {
-                if (!gI.empty()) ginst.push_back(k);
-                gI.push_back(I);
-                gpt.push_back(gpt.back() + I);
-            }
-        }
-        ginst.push_back(B);
-        const int NG = (int)gI.size();
-        const long long P = gpt.back();
-        NOP_TRY(ctx->scratch("ft_gpt", sizeof(long long) * (NG + 1), &q));
+        // instances grouped by cell count (CSR): distinct points once; the
+        // grouping depends on the batch layout only, so it is built and
+        // uploaded once per problem
+        NOP_TRY(ctx->scratch("ft_gpt", sizeof(long long) * (B + 1), &q));
         long long* gpt_d = (long long*)q;
-        NOP_TRY(ctx->scratch("ft_gint", sizeof(int) * (2 * (size_t)NG + 1 + B), &q));
+        NOP_TRY(ctx->scratch("ft_gint", sizeof(int) * (3 * (size_t)B + 1), &q));
         int* gI_d = (int*)q;
-        int* ginst_d = gI_d + NG;
-        int* list_d = ginst_d + NG + 1;
-        std::vector<int> ints(gI);
-        ints.insert(ints.end(), ginst.begin(), ginst.end());
-        ints.insert(ints.end(), order.begin(), order.end());
-        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(gpt_d, gpt.data(), sizeof(long long) * (NG + 1),
-                                          cudaMemcpyHostToDevice, ctx->stream));
-        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(gI_d, ints.data(), sizeof(int) * ints.size(),
-                                          cudaMemcpyHostToDevice, ctx->stream));
-        // per 128-point tile: first and last group, instance range
-        const long long ntile = (P + 127) / 128;
-        std::vector<int4> tinfo((size_t)ntile);
-        {
+        if (s.ft_version != s.layout_version) {
+            std::vector<int> order(B);
+            std::iota(order.begin(), order.end(), 0);
+            std::stable_sort(order.begin(), order.end(),
+                             [&](int x, int y) { return s.ncell[x] < s.ncell[y]; });
+            std::vector<long long> gpt(1, 0);
+            std::vector<int> gI, ginst(1, 0);
+            for (int k = 0; k < B; ++k) {
+                const int I = s.ncell[order[k]];
+                if (gI.empty() || gI.back() != I) {
+                    if (!gI.empty()) ginst.push_back(k);
+                    gI.push_back(I);
+                    gpt.push_back(gpt.back() + I);
+                }
+            }
+            ginst.push_back(B);
+            const int NG = (int)gI.size();
+            const long long P = gpt.back();
+            std::vector<int> ints(gI);
+            ints.insert(ints.end(), ginst.begin(), ginst.end());
+            ints.insert(ints.end(), order.begin(), order.end());
+            NOP_CUDA_TRY(ctx, cudaMemcpyAsync(gpt_d, gpt.data(), sizeof(long long) * (NG + 1),
+                                              cudaMemcpyHostToDevice, ctx->stream));
+            NOP_CUDA_TRY(ctx, cudaMemcpyAsync(gI_d, ints.data(), sizeof(int) * ints.size(),
+                                              cudaMemcpyHostToDevice, ctx->stream));
+            // per 128-point tile: first and last group, instance range
+            const long long ntile = (P + 127) / 128;
+            std::vector<int4> tinfo((size_t)ntile);
             int gg = 0;
             for (long long tt = 0; tt < ntile; ++tt) {
                 const long long p0 = tt * 128, p1 = std::min(P, p0 + 128) - 1;
@@ -624,11 +624,22 @@ int deeponet_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* sta
                 while (gpt[gl + 1] <= p1) ++gl;
                 tinfo[(size_t)tt] = make_int4(gg, gl, ginst[gg], ginst[gl + 1]);
             }
+            NOP_TRY(ctx->scratch("ft_tinfo", sizeof(int4) * (size_t)ntile, &q));
+            NOP_CUDA_TRY(ctx, cudaMemcpyAsync(q, tinfo.data(), sizeof(int4) * (size_t)ntile,
+                                              cudaMemcpyHostToDevice, ctx->stream));
+            // the host vectors go out of scope: let the copies finish (once
+            // per problem)
+            NOP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+            s.ft_groups = NG;
+            s.ft_points = P;
+            s.ft_version = s.layout_version;
         }
-        NOP_TRY(ctx->scratch("ft_tinfo", sizeof(int4) * (size_t)ntile, &q));
+        const int NG = s.ft_groups;
+        const long long P = s.ft_points;
+        int* ginst_d = gI_d + NG;
+        int* list_d = ginst_d + NG + 1;
+        NOP_TRY(ctx->scratch("ft_tinfo", sizeof(int4) * (size_t)((P + 127) / 128), &q));
         int4* tinfo_d = (int4*)q;
-        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(tinfo_d, tinfo.data(), sizeof(int4) * (size_t)ntile,
-                                          cudaMemcpyHostToDevice, ctx->stream));
         NOP_TRY(ctx->scratch("tc_err", sizeof(int), &q));
         int* err_d = (int*)q;
         NOP_CUDA_TRY(ctx, cudaMemsetAsync(err_d, 0, sizeof(int), ctx->stream));
@@ -637,13 +648,19 @@ int deeponet_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* sta
         NOP_TRY(trunk_tc_launch(ctx, P, tinfo_d, gpt_d, gI_d, ginst_d, list_d, s.cell_off_d, TW,
                                 TB, beta_keep, status, phi_d, err_d));
         ctx->phase_end(mk);
-        int herr = 0;
-        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(&herr, err_d, sizeof(int), cudaMemcpyDeviceToHost,
+        NOP_TRY(ctx->pinned("tc_err", sizeof(int), &q));
+        int* herr = (int*)q;
+        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(herr, err_d, sizeof(int), cudaMemcpyDeviceToHost,
                                           ctx->stream));
-        NOP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-        if (herr) {
-            ctx->set_error("trunk evaluation: tensor-core completion wait timed out");
-            return NOP_ETIMEOUT;
+        if (ctx->defer_tc_check) {
+            // the caller reads the flag after its own final synchronisation
+            ctx->tc_err_pending = herr;
+        } else {
+            NOP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+            if (*herr) {
+                ctx->set_error("trunk evaluation: tensor-core completion wait timed out");
+                return NOP_ETIMEOUT;
+            }
         }
         if (status_d)
             NOP_CUDA_TRY(ctx, cudaMemcpyAsync(status_d, status, sizeof(int) * B,

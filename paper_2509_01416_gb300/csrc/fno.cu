@@ -680,7 +680,11 @@ int fno_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* status_d
     NOP_CUDA_TRY(ctx, cudaMemsetAsync(flags, 0, sizeof(int) * (size_t)(4 * B + 4), ctx->stream));
     NOP_CUDA_TRY(ctx, cudaMemsetAsync(prev, 0x7f, sizeof(double) * (size_t)B, ctx->stream));
     int* active_h = nullptr;
-    NOP_CUDA_TRY(ctx, cudaMallocHost(&active_h, sizeof(int)));
+    {
+        void* ph;
+        NOP_TRY(ctx->pinned("fno_active", sizeof(int), &ph));
+        active_h = (int*)ph;
+    }
     const int imax = predict_only ? 1 : itmax;
     int rc = NOP_OK;
     for (int it = 1; it <= imax; ++it) {
@@ -704,7 +708,6 @@ int fno_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* status_d
         }
         if (*active_h == 0) break;
     }
-    cudaFreeHost(active_h);
     if (rc != NOP_OK) {
         if (ctx->err.empty()) ctx->set_error("FNO recast iteration failed");
         return rc;

@@ -421,6 +421,49 @@ int nop_no_predict(nop_ctx* ctx, const double* src, double* phi_out) {
     return NOP_OK;
 }
 
+}  // extern "C"
+
+namespace nop {
+// The recast iteration (Eq. 24) enqueued on the context stream: the
+// prediction goes to pd (device, G*C doubles); the per-instance status and
+// iteration counts (2B ints) are copied into a pinned host buffer whose
+// address comes back in *stat_h, valid once the stream is synchronised.
+int recast_enqueue(nop_ctx* ctx, double tol, int itmax, double* pd, const int** stat_h) {
+    const int B = ctx->geometry == NOP_GEOM_SLAB ? ctx->slab.n_inst : 1;
+    void* p;
+    NOP_TRY(ctx->scratch("rc_stat", sizeof(int) * 2 * B, &p));
+    int* sd = (int*)p;
+    if (is_fno(ctx)) NOP_TRY(fno_recast(ctx, tol, itmax, pd, sd, sd + B, false, nullptr));
+    else NOP_TRY(deeponet_recast(ctx, tol, itmax, pd, sd, sd + B, false, nullptr));
+    NOP_TRY(ctx->pinned("rc_stat_h", sizeof(int) * 2 * B, &p));
+    NOP_CUDA_TRY(ctx, cudaMemcpyAsync(p, sd, sizeof(int) * 2 * B, cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+    *stat_h = (const int*)p;
+    return NOP_OK;
+}
+
+// Statistics of a recast whose status buffer h (from recast_enqueue) is
+// complete: per instance NOP_OK, NOP_ENOCONV (cap reached) or NOP_EDIVERGE.
+void recast_collect(nop_ctx* ctx, const int* h, nop_stats* st, bool per_instance) {
+    const int B = ctx->geometry == NOP_GEOM_SLAB ? ctx->slab.n_inst : 1;
+    int worst = NOP_OK, imax = 0;
+    for (int b = 0; b < B; ++b) {
+        const int code = h[b] == 3 ? NOP_EDIVERGE : (h[b] == 0 ? NOP_ENOCONV : NOP_OK);
+        if (code == NOP_EDIVERGE || (code != NOP_OK && worst == NOP_OK)) worst = code;
+        imax = std::max(imax, h[B + b]);
+        if (per_instance && st && st->inst_status) st->inst_status[b] = code;
+        if (per_instance && st && st->inst_iterations) st->inst_iterations[b] = h[B + b];
+    }
+    if (st) {
+        st->recast_iterations = imax;
+        st->recast_status = worst;
+        if (per_instance) st->status = worst;
+    }
+}
+}  // namespace nop
+
+extern "C" {
+
 int nop_recast_iterate(nop_ctx* ctx, double tol, int itmax, int flags, double* phi_out,
                        nop_stats* st) {
     if (!ctx || !phi_out || !(tol > 0) || itmax < 1) return NOP_EINVAL;
@@ -429,7 +472,6 @@ int nop_recast_iterate(nop_ctx* ctx, double tol, int itmax, int flags, double* p
         ctx->set_error("the recast iteration needs a single-group problem");
         return NOP_EINVAL;
     }
-    const int B = ctx->geometry == NOP_GEOM_SLAB ? ctx->slab.n_inst : 1;
     const long long C = ctx->C;
     void* p;
     double* pd = phi_out;
@@ -437,30 +479,13 @@ int nop_recast_iterate(nop_ctx* ctx, double tol, int itmax, int flags, double* p
         NOP_TRY(ctx->scratch("rc_phi", sizeof(double) * C, &p));
         pd = (double*)p;
     }
-    NOP_TRY(ctx->scratch("rc_stat", sizeof(int) * 2 * B, &p));
-    int* sd = (int*)p;
-    if (is_fno(ctx)) NOP_TRY(fno_recast(ctx, tol, itmax, pd, sd, sd + B, false, nullptr));
-    else NOP_TRY(deeponet_recast(ctx, tol, itmax, pd, sd, sd + B, false, nullptr));
+    const int* h = nullptr;
+    NOP_TRY(nop::recast_enqueue(ctx, tol, itmax, pd, &h));
     if (!(flags & NOP_OUT_DEVICE))
         NOP_CUDA_TRY(ctx, cudaMemcpyAsync(phi_out, pd, sizeof(double) * C, cudaMemcpyDeviceToHost,
                                           ctx->stream));
-    std::vector<int> h(2 * B);
-    NOP_CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), sd, sizeof(int) * 2 * B, cudaMemcpyDeviceToHost,
-                                      ctx->stream));
     NOP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-    int worst = NOP_OK, imax = 0;
-    for (int b = 0; b < B; ++b) {
-        const int code = h[b] == 3 ? NOP_EDIVERGE : (h[b] == 0 ? NOP_ENOCONV : NOP_OK);
-        if (code == NOP_EDIVERGE || (code != NOP_OK && worst == NOP_OK)) worst = code;
-        imax = std::max(imax, h[B + b]);
-        if (st && st->inst_status) st->inst_status[b] = code;
-        if (st && st->inst_iterations) st->inst_iterations[b] = h[B + b];
-    }
-    if (st) {
-        st->recast_iterations = imax;
-        st->recast_status = worst;
-        st->status = worst;
-    }
+    nop::recast_collect(ctx, h, st, true);
     return NOP_OK;
 }
 

@@ -2,7 +2,9 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <array>
 #include <cstdint>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -53,8 +55,17 @@ struct SlabDev {
     long long C = 0;                 // total cells
     std::vector<int> ncell, order;   // host copies
     std::vector<double> width;
-    std::vector<double> cmax;        // host: largest in-group scattering ratio
+    std::vector<double> rho;         // host: estimated contraction of source iteration
     std::vector<int> last_iters;     // host: iterations of each instance in the last solve
+    // the last slab schedule and the hash of what it was computed from
+    std::vector<int> plan_small, plan_big, plan_cfg;
+    int plan_big_blocks = 0, plan_smem_cells = 1, plan_direct = 0;
+    unsigned long long plan_key = 0;
+    long long version = 0;           // bumped by every nop_set_problem
+    long long layout_version = 0;    // bumped when the cell counts or orders change
+    long long ft_version = -1;       // layout version of the trunk point grouping
+    int ft_groups = 0;
+    long long ft_points = 0;
     std::vector<int> last_iters_dsa; // the same for solves with the diffusion correction
                                      // of this batch layout (0 = unknown); the scheduler's cost
     std::vector<long long> cell_off; // host prefix sums
@@ -102,6 +113,12 @@ struct nop_ctx {
     double *sigt_d = nullptr, *sigs_d = nullptr, *src_d = nullptr, *nsf_d = nullptr,
            *chi_d = nullptr, *sigs1_d = nullptr;
 
+    // slab autotuner: per precision, bucket key -> measured microseconds of
+    // one source iteration per cell of {direct warp, chunked warp, direct
+    // team, chunked team} (-1: not measured); kept for the context's life
+    std::map<long long, std::array<double, 4>> sn1d_tune[2];
+    double last_tune_ms = 0.0;   // calibration time of the last slab solve
+    int last_direct = 0;         // instances of the last slab solve on direct lanes
     // mbarrier poll limit of the tensor-core kernels (nop_set_wait_limit);
     // negative: the library default
     long long wait_limit = -1;
@@ -132,10 +149,24 @@ struct nop_ctx {
 
     // scratch owned by the solvers (named buffers)
     std::vector<std::pair<std::string, nop::DevBuf>> bufs;
+    // pinned host buffers (named) that per-call host <-> device copies go
+    // through, so that the copies stay asynchronous; every call that fills
+    // one ends with a stream synchronisation before the next call reuses it
+    std::vector<std::pair<std::string, nop::DevBuf>> pins;
+    // a tensor-core kernel's wait-limit flag whose check is deferred to the
+    // caller's final synchronisation (pinned host int), or null
+    const int* tc_err_pending = nullptr;
+    bool defer_tc_check = false;   // set by a solve whose warm start ends in its sync
 
     void set_error(const std::string& m) { err = m; }
     // Device buffer `name` with at least `bytes` bytes (grows, contents kept undefined).
     int scratch(const char* name, size_t bytes, void** out);
+    // Pinned host buffer `name` with at least `bytes` bytes (grows after a
+    // stream synchronisation, contents kept undefined).
+    int pinned(const char* name, size_t bytes, void** out);
+    // After the stream was synchronised: NOP_ETIMEOUT if a deferred
+    // tensor-core wait-limit flag is set (and clears the pending check).
+    int check_deferred();
 };
 
 namespace nop {
@@ -156,6 +187,11 @@ int deeponet_forward_raw(nop_ctx* ctx, int n, const float* U, int P, const float
 int deeponet_backward(nop_ctx* ctx, int n, int P, const float* dout, const float* U,
                       const float* X);
 int deeponet_project(nop_ctx* ctx, const double* field_host, float* out_host);
+// The recast iteration (Eq. 24) enqueued without synchronising (no_capi.cu):
+// statistics land in a pinned buffer *stat_h, read by recast_collect after the
+// stream was synchronised.
+int recast_enqueue(nop_ctx* ctx, double tol, int itmax, double* pd, const int** stat_h);
+void recast_collect(nop_ctx* ctx, const int* stat_h, nop_stats* st, bool per_instance);
 int deeponet_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* status_d,
                     int* iters_d, bool predict_only, const double* src_d);
 int fno_forward_raw(nop_ctx* ctx, int n, const float* in, int n1, int n2, float* out, bool keep);
@@ -204,5 +240,12 @@ int xy_solve(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
              double* phi_out, bool out_dev, double* k_out, nop_stats* st);
 
 // Lane split of the 1D sweep (log2 lanes per angle group, angles per lane).
-void sn1d_pick_config(int cells, int order, int* lg_ng, int* A, bool pow2 = false);
+// team selection of the slab batch scheduler (sn1d.cu)
+int sn1d_select_teams(int n, const double* lat_w, const double* lat_t, int warps, int width,
+                      int mode, std::vector<char>& team, double* span);
+
+// lane split of the chunked layout for I cells and order N; cost_out: the
+// model's issue slots of one direction half per iteration
+void sn1d_pick_config(int cells, int order, int* lg_ng, int* A, bool pow2 = false,
+                      double* cost_out = nullptr);
 }  // namespace nop

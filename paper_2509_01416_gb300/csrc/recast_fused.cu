@@ -1,14 +1,17 @@
-// One launch per recast iteration (Sec. 5.1 Eq. 24) for the DeepONet of
-// 128 sensors, four 128-wide branch layers and 128 basis functions: split of
-// the recast source into unit-integral parts, the branch MLP on both parts,
-// the coefficients beta = sigma+ N[+] - sigma- N[-], the operator-grid flux
-// u = T_ref beta and the convergence bookkeeping of every instance.
+// The whole recast iteration (Sec. 5.1 Eq. 24) in one launch for the
+// DeepONet of 128 sensors, four 128-wide branch layers and 128 basis
+// functions.  Every iteration of an instance: split of the recast source into
+// unit-integral parts, the branch MLP on both parts, the coefficients beta =
+// sigma+ N[+] - sigma- N[-], the operator-grid flux u = T_ref beta and the
+// convergence bookkeeping.  Instances are independent, so a CTA iterates its
+// tile of 16 instances until all of them are frozen (converged, diverged) or
+// the cap is reached, with no grid-wide step in between.
 //
 // A persistent CTA per SM keeps the four branch weight matrices and T_ref in
-// shared memory as BF16 (the operand precision of the GEMM path) and walks
-// tiles of 16 instances (32 rows: the positive and negative part of each);
-// the products run on mma.sync BF16 tensor-core instructions with FP32
-// accumulation, bias and ReLU in FP32.
+// shared memory as BF16 (the operand precision of the GEMM path), staged once
+// per launch, and walks tiles of 16 instances (32 rows: the positive and
+// negative part of each); the products run on mma.sync BF16 tensor-core
+// instructions with FP32 accumulation, bias and ReLU in FP32.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -39,8 +42,7 @@ struct RfArgs {
     int* iters;
     double* prev;
     int* run;
-    int* active;                // this launch's count of still-running instances
-    int* active_next;           // zeroed here for the next launch
+    int itmax;                  // recast iterations at most
 };
 
 __device__ __forceinline__ void rf_mma(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
@@ -108,7 +110,6 @@ __global__ void __launch_bounds__(RF_THREADS, 1) recast_fused_kernel(RfArgs a) {
     int* flv = (int*)(snv + RF_NI);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (blockIdx.x == 0 && tid == 0) *a.active_next = 0;
     // stage the five BF16 matrices with 16-byte copies into padded rows
     for (int e = tid; e < 5 * RF_W * (RF_W / 8); e += RF_THREADS) {
         const int mtx = e / (RF_W * (RF_W / 8));
@@ -120,13 +121,14 @@ __global__ void __launch_bounds__(RF_THREADS, 1) recast_fused_kernel(RfArgs a) {
 
     const int gq = lane >> 2, tq = lane & 3, n0 = 16 * warp;
     const int ntiles = (a.B + RF_NI - 1) / RF_NI;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        // a tile whose instances are all frozen (converged, capped or
-        // diverged) has nothing to do
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+    for (int it = 0; it < a.itmax; ++it) {
+        // a tile whose instances are all frozen (converged or diverged) is
+        // done
         {
             const int b = tile * RF_NI + (tid & (RF_NI - 1));
             const int running = tid < RF_NI && b < a.B && a.status[b] == 0;
-            if (!__syncthreads_or(running)) continue;
+            if (!__syncthreads_or(running)) break;
         }
         // 1. recast source S + D u of two instances per warp, split into parts
 #pragma unroll
@@ -237,7 +239,6 @@ __global__ void __launch_bounds__(RF_THREADS, 1) recast_fused_kernel(RfArgs a) {
                     if (a.run[b] >= a.diverge_run) st = 3;
                 }
                 a.status[b] = st;
-                if (st == 0) atomicAdd(a.active, 1);
             }
         }
         __syncthreads();
@@ -256,8 +257,8 @@ bool recast_fused_supported(const nop_no_config& c) {
            c.basis == RF_W && c.depth == 4;
 }
 
-// The recast loop on the fused kernel.  active2: two device counters.
-// Returns the iterations run in *its.
+// The recast loop on the fused kernel (one launch).  active2: unused device
+// counters kept for the generic path's signature.  *its: the iteration cap.
 int recast_fused_run(nop_ctx* ctx, int B, double h, double tol, int itmax, const float* PS,
                      const float* PD, float* u, const float* const W[4], const float* const b[4],
                      const float* Tref, float* beta, float* beta_keep, int* status, int* iters,
@@ -291,34 +292,17 @@ int recast_fused_run(nop_ctx* ctx, int B, double h, double tol, int itmax, const
     a.iters = iters;
     a.prev = prev;
     a.run = run;
+    a.itmax = itmax;
     const int ntiles = (B + RF_NI - 1) / RF_NI;
     const int grid = std::max(1, std::min(ntiles, ctx->sm_count));
-    int* active_h = nullptr;
-    NOP_CUDA_TRY(ctx, cudaMallocHost(&active_h, sizeof(int)));
-    int rc = NOP_OK, it;
-    for (it = 1; it <= itmax; ++it) {
-        a.active = active2 + (it & 1);
-        a.active_next = active2 + ((it + 1) & 1);
-        recast_fused_kernel<<<grid, RF_THREADS, RF_SMEM, ctx->stream>>>(a);
-        if (cudaGetLastError() != cudaSuccess) {
-            rc = NOP_ECUDA;
-            break;
-        }
-        ctx->count_launch(false);
-        // converged instances are frozen: the host looks every few iterations
-        if (it % 4 != 0 && it != itmax) continue;
-        if (cudaMemcpyAsync(active_h, a.active, sizeof(int), cudaMemcpyDeviceToHost,
-                            ctx->stream) != cudaSuccess ||
-            cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
-            rc = NOP_ECUDA;
-            break;
-        }
-        if (*active_h == 0) break;
+    recast_fused_kernel<<<grid, RF_THREADS, RF_SMEM, ctx->stream>>>(a);
+    if (cudaGetLastError() != cudaSuccess) {
+        ctx->set_error("fused recast iteration failed");
+        return NOP_ECUDA;
     }
-    cudaFreeHost(active_h);
-    *its = std::min(it, itmax);
-    if (rc != NOP_OK) ctx->set_error("fused recast iteration failed");
-    return rc;
+    ctx->count_launch(false);
+    *its = itmax;
+    return NOP_OK;
 }
 
 }  // namespace nop

@@ -22,7 +22,7 @@ extern template int sn1d_run<double>(nop_ctx*, const nop_solve_opts*, bool, cons
 // Chunked splits add the map-composition pass and a scan.  A lane carries
 // A in {1, 2, 4} angles (the compiled variants; wider lanes would raise the
 // kernel's register count and cut its occupancy).
-void sn1d_pick_config(int I, int N, int* lg_out, int* A_out, bool pow2) {
+void sn1d_pick_config(int I, int N, int* lg_out, int* A_out, bool pow2, double* cost_out) {
     // A angles per lane: any count up to 6 (powers of two only when asked),
     // so that ng x A covers the half-angle set with few idle slots
     const int h = N / 2;
@@ -51,6 +51,44 @@ void sn1d_pick_config(int I, int N, int* lg_out, int* A_out, bool pow2) {
     }
     *lg_out = bl;
     *A_out = bA;
+    if (cost_out) *cost_out = best;
+}
+
+// Team selection of the slab batch scheduler (host arithmetic).  lat_w[b]:
+// latency of instance b on one warp; lat_t[b]: on a team of `width` warps
+// (< 0: no team possible).  mode 0: the instances that can have a team are
+// taken in decreasing warp latency and given one while their warp latency
+// exceeds the expected span S = (warp latencies of the warp instances +
+// width x team latencies of the team instances) / warps, S updated after
+// each; so the fewest, longest instances get teams and no instance left on a
+// warp (that could have a team) outlasts S.  mode 1: every instance that can;
+// mode 2: none.  Returns the final S in *span.
+int sn1d_select_teams(int n, const double* lat_w, const double* lat_t, int warps, int width,
+                      int mode, std::vector<char>& team, double* span) {
+    if (n < 0 || warps < 1 || width < 1 || (n > 0 && (!lat_w || !lat_t))) return NOP_EINVAL;
+    team.assign(n, 0);
+    double work = 0.0;
+    for (int b = 0; b < n; ++b) work += lat_w[b];
+    if (mode == 1) {
+        for (int b = 0; b < n; ++b)
+            if (lat_t[b] >= 0.0) {
+                team[b] = 1;
+                work += width * lat_t[b] - lat_w[b];
+            }
+    } else if (mode == 0) {
+        std::vector<int> cand;
+        for (int b = 0; b < n; ++b)
+            if (lat_t[b] >= 0.0) cand.push_back(b);
+        std::stable_sort(cand.begin(), cand.end(),
+                         [&](int x, int y) { return lat_w[x] > lat_w[y]; });
+        for (int b : cand) {
+            if (!(lat_w[b] > work / warps)) break;
+            team[b] = 1;
+            work += width * lat_t[b] - lat_w[b];
+        }
+    }
+    if (span) *span = work / warps;
+    return NOP_OK;
 }
 
 int sn1d_solve(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* phi0,

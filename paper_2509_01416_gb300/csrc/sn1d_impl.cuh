@@ -30,7 +30,11 @@
 // diffusion system once per solve, and dsa_pass solves it after each sweep on
 // one warp.
 #include <algorithm>
+#include <array>
+#include <chrono>
 #include <cmath>
+#include <cstring>
+#include <map>
 #include <numeric>
 
 #pragma once
@@ -650,6 +654,266 @@ __device__ double si_iteration(const Sn1dArgs& a, const Grp& gr, const Stage<T>&
     return sn > 0.0 ? sqrt(sd / sn) : (sd > 0.0 ? INFINITY : 0.0);
 }
 
+// ------------------------------------------------------------ direct lanes
+// Direct-lane sweep of slabs with vacuum faces and isotropic scattering: the
+// two direction halves are independent within a source iteration (each sees
+// vacuum inflow and the emission of the previous iterate), so they run at
+// the same time.  Lanes 0-15 carry mu < 0 (cells right to left), lanes 16-31
+// mu > 0 (left to right); lane j of a half carries the half-angles
+// j, j + 16, ..., A of them.  On one warp every lane walks the whole slab: no
+// chunk maps and no scan, so each cell-angle update is one pass of the
+// compensated diamond-difference increment.  A team of W warps (a whole
+// block) splits the cells into W chunks, composes each chunk's affine map
+// psi_out = (1 - D) psi_in + B per chain, and hands the entry fluxes across
+// chunks through shared memory before the sweep.
+//
+// Cells stream through a double-buffered ring of R = 32 staged {sigma_t, s}
+// pairs per direction (s = emission of the current iterate), loaded one
+// block of R cells ahead with coalesced 16-byte loads.  The step loop is
+// software-pipelined: the staged operands and the reciprocal of step k + 1
+// are formed during step k, so a step's dependent chain is the flux update
+// alone.  The angle sums go through a second ring: at step k lane l stores
+// its partial sum in row l, slot k mod R (row pitch R + 1: no bank
+// conflicts), and every R steps lane l adds the 16 rows of each half for
+// slot l.  Step k reaches cell c0 + k going right and c0 + len - 1 - k going
+// left, so a cell is reached twice; the half sum that arrives first waits
+// in a pair buffer (shared memory, or the instance's U cells when the chunk
+// is long), and the second arrival completes the cell: new flux, change and
+// norm terms (the old flux comes from the staging load of the same cell).
+constexpr int DR = 32;   // ring length (cells per staged block)
+constexpr int DSLAB = SN1D_STAGE_BYTES / (SN1D_THREADS / 32);   // shared bytes per warp
+
+// Per-warp shared-memory layout of the direct path inside the warp's slab:
+// staging ring, partial-sum ring, chunk maps (team path), pair buffer.
+template <typename T>
+struct DirectSmem {
+    Cell2<T>* stg;   // [2 dir][2 buf][DR + 2]
+    T* red;          // [32][DR + 1]
+    T* maps;         // [32 lanes][4][2] chunk maps (team path)
+    Cell2<T>* pair;  // first-arrival half sums {mu > 0, mu < 0}
+    int pair_cap;    // entries of pair
+    __device__ static DirectSmem at(unsigned char* slab) {
+        DirectSmem s;
+        s.stg = (Cell2<T>*)slab;
+        s.red = (T*)(slab + 4 * (DR + 2) * sizeof(Cell2<T>));
+        s.maps = s.red + 32 * (DR + 1);
+        s.pair = (Cell2<T>*)(s.maps + 32 * 4 * 2);
+        s.pair_cap = (int)((slab + DSLAB - (unsigned char*)s.pair) / sizeof(Cell2<T>));
+        return s;
+    }
+};
+
+// Loads the X entries of the two cells lane l stages for block kb of the
+// chunk [c0, c0 + len): mu > 0 reads c0 + kb R + l, mu < 0 reads
+// c0 + len - 1 - (kb R + l).
+template <typename T>
+__device__ __forceinline__ void direct_fetch(const Cell4<T>* X, int c0, int len, int kb, int l,
+                                             Cell4<T>& vp, Cell4<T>& vm) {
+    const int k = kb * DR + l;
+    if (k < len) {
+        vp = X[c0 + k];
+        vm = X[c0 + len - 1 - k];
+    }
+}
+
+// Stages the fetched cells into buffer `buf` and keeps their old fluxes.
+template <typename T>
+__device__ __forceinline__ void direct_stage(const DirectSmem<T>& sm, int buf, int l,
+                                             const Cell4<T>& vp, const Cell4<T>& vm, T& php,
+                                             T& phm) {
+    Cell2<T> p, m;
+    p.s0 = vp.st;
+    p.s1 = vp.y * vp.phi + vp.z;
+    m.s0 = vm.st;
+    m.s1 = vm.y * vm.phi + vm.z;
+    sm.stg[(2 + buf) * (DR + 2) + l] = p;   // mu > 0 rows: 2, 3
+    sm.stg[buf * (DR + 2) + l] = m;         // mu < 0 rows: 0, 1
+    php = vp.phi;
+    phm = vm.phi;
+}
+
+// One pass over this warp's chunk [c0, c0 + len) for all its chains.
+// COMPOSE: build the chunk map (D, B) of every chain.  Otherwise sweep from
+// psi_in, complete every cell of the chunk (new flux into X, change and
+// norm terms into acc_d, acc_n).
+template <typename T, int A, bool COMPOSE>
+__device__ __forceinline__ void direct_pass(const DirectSmem<T>& sm, Cell4<T>* X, Cell2<T>* U,
+                                            int c0, int len, const T (&cc)[A], const T (&wt)[A],
+                                            CSum<T> (&psi)[A], T (&D)[A], T& acc_d, T& acc_n) {
+    const int lane = threadIdx.x & 31;
+    const int half = lane >> 4;   // 0: mu < 0, 1: mu > 0
+    Cell2<T>* pair = ((len + 1) / 2 <= sm.pair_cap) ? sm.pair : U + c0;
+    Cell4<T> vp{}, vm{};
+    T php = T(0), phm = T(0);
+    direct_fetch<T>(X, c0, len, 0, lane, vp, vm);
+    direct_stage<T>(sm, 0, lane, vp, vm, php, phm);
+    __syncwarp();
+    const int nblk = (len + DR - 1) / DR;
+    const Cell2<T>* row = sm.stg + 2 * half * (DR + 2);
+    T* myred = sm.red + lane * (DR + 1);
+#pragma unroll 1
+    for (int kb = 0; kb < nblk; ++kb) {
+        // the next block's cells, in flight during this block's steps
+        direct_fetch<T>(X, c0, len, kb + 1, lane, vp, vm);
+        const int nk = min(DR, len - kb * DR);
+        const Cell2<T>* cur = row + (kb & 1) * (DR + 2);
+        // two-deep pipeline: step k loads the operands of step k + 2 and
+        // forms the reciprocals of step k + 1 (slots DR, DR + 1 are padding)
+        Cell2<T> v0 = cur[0], v1 = cur[1];
+        T r0[A];
+#pragma unroll
+        for (int q = 0; q < A; ++q) r0[q] = rcp_dd(cc[q] + v0.s0);
+        // two steps per loop trip: the independent work of consecutive steps
+        // (operands, reciprocals, angle sums) interleaves with the flux chain
+#pragma unroll 2
+        for (int k = 0; k < nk; ++k) {
+            const T st = v0.s0, s = v0.s1;
+            T r[A];
+#pragma unroll
+            for (int q = 0; q < A; ++q) r[q] = r0[q];
+            const Cell2<T> v2 = cur[k + 2];
+#pragma unroll
+            for (int q = 0; q < A; ++q) r0[q] = rcp_dd(cc[q] + v1.s0);
+            v0 = v1;
+            v1 = v2;
+            if constexpr (COMPOSE) {
+#pragma unroll
+                for (int q = 0; q < A; ++q) {
+                    const T r2 = T(2) * r[q];
+                    D[q] = (r2 * st) * (T(1) - D[q]) + D[q];
+                    psi[q].add(r2 * (s - st * psi[q].hi));
+                }
+            } else {
+                T p = T(0);
+#pragma unroll
+                for (int q = 0; q < A; ++q) {
+                    const T dl = r[q] * (s - st * psi[q].hi);
+                    p += wt[q] * (psi[q].hi + (dl + psi[q].lo));
+                    psi[q].add(dl + dl);
+                }
+                myred[k] = p;
+            }
+        }
+        __syncwarp();
+        if constexpr (!COMPOSE) {
+            // slot `lane` of this block: step k reaches cell c0 + k (mu > 0)
+            // and cell c0 + len - 1 - k (mu < 0)
+            const int k = kb * DR + lane;
+            const bool valid = lane < nk;
+            const int twice = 2 * k - (len - 1);   // < 0 first arrival, > 0 second, 0 middle
+            T sp = T(0), sn = T(0);
+            if (valid) {
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    sn += sm.red[r * (DR + 1) + lane];
+                    sp += sm.red[(16 + r) * (DR + 1) + lane];
+                }
+                if (twice < 0) {
+                    Cell2<T> fp;
+                    fp.s0 = sp;
+                    fp.s1 = sn;
+                    pair[k] = fp;
+                }
+            }
+            __syncwarp();
+            if (valid && twice >= 0) {
+                T fpn, fmn;
+                if (twice == 0) {
+                    fpn = sp + sn;
+                    fmn = fpn;
+                } else {
+                    const Cell2<T> o = pair[len - 1 - k];
+                    fpn = sp + o.s1;
+                    fmn = sn + o.s0;
+                }
+                const T dp = fpn - php;
+                acc_d += dp * dp;
+                acc_n += fpn * fpn;
+                X[c0 + k].phi = fpn;
+                if (twice > 0) {
+                    const T dm = fmn - phm;
+                    acc_d += dm * dm;
+                    acc_n += fmn * fmn;
+                    X[c0 + len - 1 - k].phi = fmn;
+                }
+            }
+        }
+        if (kb + 1 < nblk) direct_stage<T>(sm, (kb + 1) & 1, lane, vp, vm, php, phm);
+        __syncwarp();
+    }
+}
+
+// One source iteration over all groups on the direct lanes; returns the
+// relative L2 change.  Team path (gr.block): warp w owns cells
+// [w m, min(I, (w + 1) m)), m = ceil(I / W).
+template <typename T, int A>
+__device__ double si_iteration_direct(const Sn1dArgs& a, const Grp& gr, unsigned char* smem,
+                                      long long off, int I, const T (&cc)[A],
+                                      const T (&wt)[A]) {
+    const int lane = threadIdx.x & 31;
+    const int half = lane >> 4;
+    const int W = gr.block ? gr.nwarps : 1;
+    const int w = gr.block ? gr.warp : 0;
+    const int m = (I + W - 1) / W;
+    const int c0 = min(I, w * m);
+    const int len = max(0, min(I, c0 + m) - c0);
+    // every warp works in its own slab of the block's shared memory (on the
+    // team path warp w of the block is chunk w)
+    const DirectSmem<T> sm = DirectSmem<T>::at(smem + (threadIdx.x >> 5) * DSLAB);
+    T acc_d = T(0), acc_n = T(0);
+    for (int g = 0; g < a.G; ++g) {
+        if (a.G > 1) {
+            group_source<T>(a, gr, off, I, g);
+            gr.sync();
+        }
+        Cell4<T>* X = (Cell4<T>*)a.X + (long long)g * a.C + off;
+        Cell2<T>* U = (Cell2<T>*)a.U + off;
+        CSum<T> psi[A];
+        T D[A];
+#pragma unroll
+        for (int q = 0; q < A; ++q) {
+            psi[q].set(T(0));
+            D[q] = T(0);
+        }
+        if (W > 1) {
+            // chunk maps, then the entry flux of every chain: vacuum at the
+            // face, then the maps of the chunks upstream in sweep order
+            direct_pass<T, A, true>(sm, X, U, c0, len, cc, wt, psi, D, acc_d, acc_n);
+#pragma unroll
+            for (int q = 0; q < A; ++q) {
+                sm.maps[(lane * 4 + q) * 2 + 0] = D[q];
+                sm.maps[(lane * 4 + q) * 2 + 1] = psi[q].val();
+            }
+            gr.sync();
+            T in[A];
+#pragma unroll
+            for (int q = 0; q < A; ++q) in[q] = T(0);
+            for (int u = 0; u < W - 1; ++u) {
+                // mu > 0: chunks 0 .. w-1 in order; mu < 0: chunks W-1 .. w+1
+                const int wu = half ? u : W - 1 - u;
+                if (half ? (wu < w) : (wu > w)) {
+                    const DirectSmem<T> su = DirectSmem<T>::at(smem + wu * DSLAB);
+#pragma unroll
+                    for (int q = 0; q < A; ++q) {
+                        const T Du = su.maps[(lane * 4 + q) * 2 + 0];
+                        const T Bu = su.maps[(lane * 4 + q) * 2 + 1];
+                        in[q] = (in[q] + Bu) - Du * in[q];
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < A; ++q) psi[q].set(in[q]);
+        }
+        direct_pass<T, A, false>(sm, X, U, c0, len, cc, wt, psi, D, acc_d, acc_n);
+        // the next group's source (and the next iteration's staging) reads
+        // the fluxes of the whole instance
+        gr.sync();
+    }
+    const double sd = gr.sum((double)acc_d);
+    const double sn = gr.sum((double)acc_n);
+    return sn > 0.0 ? sqrt(sd / sn) : (sd > 0.0 ? INFINITY : 0.0);
+}
+
 // production integral sum nsf * phi * dx over the instance (FP64)
 template <typename T>
 __device__ double production(const Sn1dArgs& a, const Grp& gr, long long off, int I, double dx) {
@@ -664,9 +928,9 @@ __device__ double production(const Sn1dArgs& a, const Grp& gr, long long off, in
     return gr.sum(acc) * dx;
 }
 
-template <typename T, int A, bool P1>
+template <typename T, int A, bool P1, bool DIRECT = false>
 __device__ void solve_instance(const Sn1dArgs& a, const Grp& gr, const Stage<T>& sg, int inst,
-                               int lg) {
+                               int lg, unsigned char* smem = nullptr) {
     const int lane = threadIdx.x & 31;
     const int j = lane & ((1 << lg) - 1);
     const int I = a.ncell[inst];
@@ -685,8 +949,9 @@ __device__ void solve_instance(const Sn1dArgs& a, const Grp& gr, const Stage<T>&
     P1Op<T, A> an{};
 #pragma unroll
     for (int q = 0; q < A; ++q) {
-        const int hi = hb + j * A + q;
-        if (hi < he) {
+        // direct lanes: lane j of each half carries half-angles j, j + 16, ...
+        const int hi = DIRECT ? (lane & 15) + 16 * q : hb + j * A + q;
+        if (hi < (DIRECT ? h : he)) {
             cc[q] = (T)(2.0 * a.mu[q0 + h + hi] / dxv);
             wt[q] = (T)a.w[q0 + h + hi];
             an.mua[q] = (T)a.mu[q0 + h + hi];
@@ -706,9 +971,13 @@ __device__ void solve_instance(const Sn1dArgs& a, const Grp& gr, const Stage<T>&
     double change = 0.0;
     int its = 0, n = 0;
     double k = 0.0, dphi = INFINITY;
+    auto iterate = [&]() -> double {
+        if constexpr (DIRECT) return si_iteration_direct<T, A>(a, gr, smem, off, I, cc, wt);
+        else return si_iteration<T, A, P1>(a, gr, sg, inst, off, I, h, hb, he, lg, cc, wt, an);
+    };
     if (!a.eigen) {
         for (its = 1; its <= a.itmax; ++its) {
-            change = si_iteration<T, A, P1>(a, gr, sg, inst, off, I, h, hb, he, lg, cc, wt, an);
+            change = iterate();
             if (!isfinite(change)) {
                 status = NOP_ENAN;
                 break;
@@ -755,8 +1024,7 @@ __device__ void solve_instance(const Sn1dArgs& a, const Grp& gr, const Stage<T>&
             gr.sync();
             int it;
             for (it = 1; it <= a.itmax_inner; ++it) {
-                change = si_iteration<T, A, P1>(a, gr, sg, inst, off, I, h, hb, he, lg, cc, wt,
-                                                an);
+                change = iterate();
                 if (!isfinite(change)) {
                     status = NOP_ENAN;
                     break;
@@ -817,10 +1085,22 @@ __device__ void solve_instance(const Sn1dArgs& a, const Grp& gr, const Stage<T>&
     gr.sync();
 }
 
+// cfg of an instance: (log2 ng) << 8 | A for the chunked lanes, or
+// SN1D_DIRECT | A for the direct lanes (A in 1..4)
+#define SN1D_DIRECT 0x10000
 template <typename T>
 __device__ __forceinline__ void dispatch(const Sn1dArgs& a, const Grp& gr, const Stage<T>& sg,
-                                         int inst) {
+                                         int inst, unsigned char* smem) {
     const int cfg = a.cfg[inst];
+    if (cfg & SN1D_DIRECT) {
+        switch (cfg & 0xff) {
+            case 1: solve_instance<T, 1, false, true>(a, gr, sg, inst, 0, smem); break;
+            case 2: solve_instance<T, 2, false, true>(a, gr, sg, inst, 0, smem); break;
+            case 3: solve_instance<T, 3, false, true>(a, gr, sg, inst, 0, smem); break;
+            default: solve_instance<T, 4, false, true>(a, gr, sg, inst, 0, smem); break;
+        }
+        return;
+    }
     const int A = cfg & 0xff, lg = cfg >> 8;
     // anisotropic instances take A in {1, 2, 4} only (the host picks so)
     switch (A) {
@@ -875,7 +1155,7 @@ __device__ void drain_big(const Sn1dArgs& a, double* red, int* job, unsigned cha
         const int jb = *job;
         __syncthreads();
         if (jb >= a.n_big) break;
-        dispatch<T>(a, gb, sg, a.big_list[jb]);
+        dispatch<T>(a, gb, sg, a.big_list[jb], smem_raw);
     }
     __syncthreads();
 }
@@ -917,7 +1197,7 @@ __global__ void __launch_bounds__(SN1D_THREADS, SN1D_BLOCKS_PER_SM) sn1d_kernel(
         // the warp's slab, free between sweeps, holds its correction's work values
         sw.scratch = (T*)((Cell2<T>*)smem_raw + (threadIdx.x >> 5) * slab);
         sw.scratch_words = slab * 2;
-        dispatch<T>(a, gw, sw, inst);
+        dispatch<T>(a, gw, sw, inst, smem_raw);
     }
     if (a.n_big > 0 && !big_first) {
         __syncthreads();
@@ -1195,128 +1475,35 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
         trace_d = (unsigned long long*)p;
     }
 
-    // ---- scheduling (host side).  Estimated work of an instance: cells x
-    // angles x iterations; the iterations are those of the previous solve of
-    // the same batch layout when known, else estimated from the largest
-    // in-group scattering ratio c (source iteration contracts roughly like c).
+    // ---- the arguments of every launch; the instance lists, lane
+    // configurations and queue split are filled in by the scheduling below
     const int blocks_max = ctx->sm_count * SN1D_BLOCKS_PER_SM;
-    const double tol_its = eigen ? std::min(o->tol_inner, o->tol) : o->tol;
-    // iterations of the previous solve of this layout, kept apart for solves
-    // with and without the diffusion correction (they differ several times)
-    std::vector<int>& last = dsa ? s.last_iters_dsa : s.last_iters;
-    std::vector<double> cost(B);
-    double total_cost = 0;
-    for (int b = 0; b < B; ++b) {
-        const double c = std::min(0.999, std::max(0.2, s.cmax[b]));
-        double its = std::min(5000.0, std::max(5.0, std::log(tol_its) / std::log(c)));
-        // the accelerated iteration contracts like about c/4 (Fourier analysis)
-        if (dsa) its = std::max(3.0, std::log(tol_its) / std::log(std::max(0.05, 0.25 * c)));
-        if (!eigen && b < (int)last.size() && last[b] > 0) its = last[b];
-        cost[b] = (double)s.ncell[b] * s.order[b] * its * G;
-        total_cost += cost[b];
-    }
-    const int max_smem_cells =
-        (int)(SN1D_STAGE_BYTES / (sizeof(Cell2<T>) + (SN1D_THREADS / 32) * sizeof(T)));
-    const int warps_total =
-        (int)std::max<long long>(1, std::min<long long>(B, (long long)blocks_max * (SN1D_THREADS / 32)));
-    // Latency of an instance on one warp: iterations x sequential cell steps
-    // per iteration of its lane split (4 passes of ceil(I/nt) steps when the
-    // cells are chunked, 2 otherwise).  With longest-first scheduling the
-    // batch takes about max(mean warp load, longest latency); an instance
-    // whose latency is above the mean warp load runs on a whole block (12
-    // warps), which cuts its latency several times at the price of about 1.5x
-    // its SM time on one warp (measured on the 4096-slab batch: thresholds
-    // of 0.5-1.5x the mean load gave 33-34, 28.8 and 30-33 ms).
-    // the correction runs on one warp: 4 passes over ceil((I+1)/32) edges
-    auto dsa_steps = [&](int b) { return dsa ? 4.0 * ((s.ncell[b] + 32) / 32) * G : 0.0; };
-    std::vector<int> cfg(B), small, big;
-    std::vector<double> lat(B);
-    double lat_sum = 0, big_work = 0, small_work = 0;
-    for (int b = 0; b < B; ++b) {
-        int lg, A;
-        sn1d_pick_config(s.ncell[b], s.order[b], &lg, &A, p1 || sizeof(T) == 8);
-        cfg[b] = (lg << 8) | A;
-        const int nt = 32 >> lg;
-        const double steps = (nt > 1 ? 4.0 : 2.0) * ((s.ncell[b] + nt - 1) / nt) * G + dsa_steps(b);
-        lat[b] = cost[b] / ((double)s.ncell[b] * s.order[b] * G) * steps;
-        lat_sum += lat[b];
-    }
-    const double mean_load = lat_sum / warps_total;
-
-    int smem_cells = 1;
-    for (int b = 0; b < B; ++b) {
-        const int h = s.order[b] / 2;
-        const bool fits = s.ncell[b] <= max_smem_cells && !p1;
-        const bool is_big =
-            fits && (o->schedule == NOP_SCHED_BLOCK ||
-                     (o->schedule == NOP_SCHED_AUTO && B > 1 && lat[b] > mean_load));
-        if (is_big) {
-            int lg, A;
-            const int hw = (h + SN1D_THREADS / 32 - 1) / (SN1D_THREADS / 32);
-            sn1d_pick_config(s.ncell[b], 2 * hw, &lg, &A, sizeof(T) == 8);
-            cfg[b] = (lg << 8) | A;
-            big.push_back(b);
-            smem_cells = std::max(smem_cells, s.ncell[b]);
-            // latency on the block: the same iterations over its lane split
-            const int nt = 32 >> lg;
-            lat[b] = cost[b] / ((double)s.ncell[b] * s.order[b] * G) *
-                     ((nt > 1 ? 4.0 : 2.0) * ((s.ncell[b] + nt - 1) / nt) * G + dsa_steps(b));
-            big_work += lat[b];
-        } else {
-            small.push_back(b);
-            small_work += lat[b] / (SN1D_THREADS / 32);
-        }
-        cost[b] = lat[b];
-    }
-    // Large and small instances run side by side from the start: a share of
-    // the blocks proportional to the large instances' block-time takes the
-    // large queue first, the other blocks go straight to the small queue.
-    int big_blocks = 0;
-    if (!big.empty()) {
-        const double share = big_work / std::max(1e-30, big_work + small_work);
-        big_blocks = (int)std::ceil(share * blocks_max);
-        big_blocks = std::max(1, std::min<int>(big_blocks, (int)big.size()));
-        if (small.empty()) big_blocks = std::min<int>(blocks_max, (int)big.size());
-    }
-    auto longest_first = [&](int x, int y) { return cost[x] > cost[y]; };
-    std::stable_sort(small.begin(), small.end(), longest_first);
-    std::stable_sort(big.begin(), big.end(), longest_first);
-    std::vector<double> k0h(B, 1.0);
-    if (k0)
-        for (int b = 0; b < B; ++b) k0h[b] = k0[b] > 0 ? k0[b] : 1.0;
-    if (!small.empty())
-        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(order_d, small.data(), sizeof(int) * small.size(),
-                                          cudaMemcpyHostToDevice, ctx->stream));
-    if (!big.empty())
-        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(big_d, big.data(), sizeof(int) * big.size(),
-                                          cudaMemcpyHostToDevice, ctx->stream));
-    NOP_CUDA_TRY(ctx, cudaMemcpyAsync(cfg_d, cfg.data(), sizeof(int) * B,
-                                      cudaMemcpyHostToDevice, ctx->stream));
-    NOP_CUDA_TRY(ctx, cudaMemcpyAsync(k0_d, k0h.data(), sizeof(double) * B,
-                                      cudaMemcpyHostToDevice, ctx->stream));
-    NOP_CUDA_TRY(ctx, cudaMemsetAsync(counter, 0, 2 * sizeof(int), ctx->stream));
-
+    constexpr int NW = SN1D_THREADS / 32;
     const long long total = (long long)G * C;
     const int pblocks = (int)std::min<long long>((total + 255) / 256, 4LL * ctx->sm_count * 8);
-    int mk = ctx->phase_begin(2);
-    sn1d_prepare<T><<<std::max(1, pblocks), 256, 0, ctx->stream>>>(
-        C, G, ctx->sigt_d, ctx->sigs_d, eigen ? nullptr : ctx->src_d,
-        eigen ? ctx->nsf_d : nullptr, phi0, (eigen && !phi0) ? 1 : 0, X, scat, ext, nsf,
-        p1 ? ctx->sigs1_d : nullptr, y1, cur);
-    NOP_CUDA_TRY(ctx, cudaGetLastError());
-    ctx->phase_end(mk);
-    ctx->count_launch(false);
-
+    auto prepare = [&]() -> int {
+        const int m = ctx->phase_begin(2);
+        sn1d_prepare<T><<<std::max(1, pblocks), 256, 0, ctx->stream>>>(
+            C, G, ctx->sigt_d, ctx->sigs_d, eigen ? nullptr : ctx->src_d,
+            eigen ? ctx->nsf_d : nullptr, phi0, (eigen && !phi0) ? 1 : 0, X, scat, ext, nsf,
+            p1 ? ctx->sigs1_d : nullptr, y1, cur);
+        NOP_CUDA_TRY(ctx, cudaGetLastError());
+        ctx->phase_end(m);
+        ctx->count_launch(false);
+        return NOP_OK;
+    };
+    NOP_TRY(prepare());
+    int mk;
     Sn1dArgs a;
     a.n_inst = B;
     a.G = G;
     a.C = C;
     a.order_list = order_d;
-    a.n_small = (int)small.size();
+    a.n_small = 0;
     a.big_list = big_d;
-    a.n_big = (int)big.size();
-    a.big_blocks = big_blocks;
-    a.smem_cells = smem_cells;
+    a.n_big = 0;
+    a.big_blocks = 0;
+    a.smem_cells = 1;
     a.counter = counter;
     a.cell_off = s.cell_off_d;
     a.ncell = s.ncell_d;
@@ -1358,10 +1545,6 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
     a.k_out = kk_d;
     a.outer_out = outer_d;
     a.trace = trace_d;
-    const int blocks = (int)std::max<long long>(
-        1, std::min<long long>(blocks_max, (long long)big.size() +
-                                               ((long long)small.size() + SN1D_THREADS / 32 - 1) /
-                                                   (SN1D_THREADS / 32)));
     const size_t smem = SN1D_STAGE_BYTES;
     NOP_CUDA_TRY(ctx, cudaFuncSetAttribute(sn1d_kernel<T>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1374,11 +1557,300 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
         ctx->phase_end(mk);
         ctx->count_launch(false);
     }
+    // Launch of the persistent kernel over given queues (warp queue `sm`,
+    // team queue `bg`, the first `bblocks` blocks starting on the team queue).
+    // The lists travel through a pinned buffer, so that the copies stay
+    // asynchronous (a copy from pageable memory can wait for the stream).
+    void* pin;
+    NOP_TRY(ctx->pinned("sn1d_lists", sizeof(int) * 3 * (size_t)B + sizeof(double) * B, &pin));
+    int* lists_h = (int*)pin;
+    double* k0_h = (double*)(lists_h + 3 * (size_t)B);
+    auto launch = [&](const Sn1dArgs& base, const std::vector<int>& sm, const std::vector<int>& bg,
+                      int bblocks, const std::vector<int>& cfgv, int smem_cells) -> int {
+        std::copy(sm.begin(), sm.end(), lists_h);
+        std::copy(bg.begin(), bg.end(), lists_h + B);
+        std::copy(cfgv.begin(), cfgv.end(), lists_h + 2 * (size_t)B);
+        if (!sm.empty())
+            NOP_CUDA_TRY(ctx, cudaMemcpyAsync(order_d, lists_h, sizeof(int) * sm.size(),
+                                              cudaMemcpyHostToDevice, ctx->stream));
+        if (!bg.empty())
+            NOP_CUDA_TRY(ctx, cudaMemcpyAsync(big_d, lists_h + B, sizeof(int) * bg.size(),
+                                              cudaMemcpyHostToDevice, ctx->stream));
+        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(cfg_d, lists_h + 2 * (size_t)B, sizeof(int) * B,
+                                          cudaMemcpyHostToDevice, ctx->stream));
+        NOP_CUDA_TRY(ctx, cudaMemsetAsync(counter, 0, 2 * sizeof(int), ctx->stream));
+        Sn1dArgs la = base;
+        la.n_small = (int)sm.size();
+        la.n_big = (int)bg.size();
+        la.big_blocks = bblocks;
+        la.smem_cells = smem_cells;
+        const int blocks = (int)std::max<long long>(
+            1, std::min<long long>(blocks_max,
+                                   (long long)bg.size() + ((long long)sm.size() + NW - 1) / NW));
+        sn1d_kernel<T><<<blocks, SN1D_THREADS, smem, ctx->stream>>>(la);
+        NOP_CUDA_TRY(ctx, cudaGetLastError());
+        ctx->count_launch(true);
+        return NOP_OK;
+    };
+
+    // ---- scheduling (host side).  Estimated iterations of an instance: those
+    // of the previous solve of the same batch layout when known (unless the
+    // caller asks for a cold schedule), else log(tol) / log(rho) with rho the
+    // estimated contraction of set-up (rho_kernel), scaled by 1.3 (the median
+    // ratio of measured to estimated counts on the 4096-slab batch).
+    const double tol_its = eigen ? std::min(o->tol_inner, o->tol) : o->tol;
+    // iterations of the previous solve of this layout, kept apart for solves
+    // with and without the diffusion correction (they differ several times)
+    std::vector<int>& last = dsa ? s.last_iters_dsa : s.last_iters;
+    const bool cold = (o->flags & NOP_COLD_SCHEDULE) != 0;
+    std::vector<double> its_est(B);
+    for (int b = 0; b < B; ++b) {
+        const double c = std::min(0.9999, std::max(0.05, s.rho[b]));
+        double its = std::min(5000.0, std::max(5.0, 1.3 * std::log(tol_its) / std::log(c)));
+        // the accelerated iteration contracts like about c/4 (Fourier analysis)
+        if (dsa) its = std::max(3.0, std::log(tol_its) / std::log(std::max(0.05, 0.25 * c)));
+        if (!eigen && !cold && b < (int)last.size() && last[b] > 0) its = last[b];
+        its_est[b] = its;
+    }
+    const int max_smem_cells =
+        (int)(SN1D_STAGE_BYTES / (sizeof(Cell2<T>) + NW * sizeof(T)));
+    const int warps_total =
+        (int)std::max<long long>(1, std::min<long long>(B, (long long)blocks_max * NW));
+    const bool direct_ok = !p1 && !dsa && !ctx->bc[0] && !ctx->bc[1] &&
+                           !(o->flags & NOP_SWEEP_CHUNKED);
+    auto direct_A = [&](int b) { return (s.order[b] / 2 + 15) / 16; };
+    auto chunked_cfg = [&](int b, bool team_cfg, double* half) {
+        int lg, A;
+        const int N = team_cfg ? 2 * ((s.order[b] / 2 + NW - 1) / NW) : s.order[b];
+        sn1d_pick_config(s.ncell[b], N, &lg, &A, p1 || sizeof(T) == 8, half);
+        return (lg << 8) | A;
+    };
+    // The schedule is a pure function of the batch, the options and (unless
+    // cold) the iteration counts of the previous solve: reuse the last one
+    // when none of these changed.
+    auto plan_key = [&]() {
+        unsigned long long key = 1469598103934665603ull;   // FNV-1a over the inputs
+        auto mix = [&](unsigned long long v) { key = (key ^ v) * 1099511628211ull; };
+        mix((unsigned long long)s.version);
+        mix(sizeof(T));
+        mix(eigen ? 1 : 0);
+        mix((unsigned long long)(o->flags & (NOP_DSA | NOP_SWEEP_CHUNKED | NOP_COLD_SCHEDULE)));
+        mix((unsigned long long)o->schedule);
+        mix((unsigned long long)ctx->bc[0] * 2 + ctx->bc[1]);
+        mix(p1 ? 1 : 0);
+        double t = tol_its;
+        unsigned long long u;
+        std::memcpy(&u, &t, sizeof(u));
+        mix(u);
+        mix((unsigned long long)ctx->sn1d_tune[sizeof(T) == 8 ? 1 : 0].size());
+        if (!cold && !eigen)
+            for (int b = 0; b < B && b < (int)last.size(); ++b) mix((unsigned long long)last[b]);
+        return key;
+    };
+    const unsigned long long key = plan_key();
+    std::vector<int> cfg, small, big;
+    int big_blocks = 0, smem_cells = 1;
+    ctx->last_tune_ms = 0.0;
+    const bool plan_hit = key == s.plan_key && (int)s.plan_cfg.size() == B;
+    if (plan_hit) {
+        cfg = s.plan_cfg;
+        small = s.plan_small;
+        big = s.plan_big;
+        big_blocks = s.plan_big_blocks;
+        smem_cells = s.plan_smem_cells;
+        ctx->last_direct = s.plan_direct;
+    } else {
+        // Per instance: the configuration and latency of one iteration on one
+        // warp (cw, lw) and on a 12-warp team (ct, lt; lt < 0: no team).
+        std::vector<int> cw(B), ct(B, 0);
+        std::vector<double> lw(B), lt(B, -1.0);
+        auto fits_team = [&](int b) { return s.ncell[b] <= max_smem_cells && !p1; };
+        const bool tune = o->schedule == NOP_SCHED_AUTO && B >= NOP_SCHED_TUNE_MIN;
+        if (tune) {
+            // ---- measured costs (the autotuner).  Every instance falls in a
+            // bucket (order, half-octave of its cell count, groups, and whether
+            // the correction, anisotropic scattering and the direct lanes apply).
+            // For every candidate layout -- direct or chunked lanes, on one warp
+            // or on a team -- the context keeps the measured time of one source
+            // iteration per cell, under the load of a full batch.  Buckets not
+            // measured yet on this device are measured now: up to 12 instances
+            // of each run 3 source iterations in one launch per candidate, timed
+            // per instance on the device clock, and the bucket keeps the median.
+            auto key_of = [&](int b) -> long long {
+                const int ib = (int)std::floor(2.0 * std::log2((double)s.ncell[b]));
+                return ((((long long)s.order[b] * 64 + ib) * 64 + G) * 8) + (dsa ? 1 : 0) +
+                       (p1 ? 2 : 0) + (direct_ok ? 4 : 0);
+            };
+            auto& table = ctx->sn1d_tune[sizeof(T) == 8 ? 1 : 0];
+            std::map<long long, std::vector<int>> todo;
+            for (int b = 0; b < B; ++b) {
+                const long long key = key_of(b);
+                if (table.count(key)) continue;
+                auto& v = todo[key];
+                if ((int)v.size() < 12) v.push_back(b);
+            }
+            if (!todo.empty()) {
+                const auto t0 = std::chrono::steady_clock::now();
+                void* tp;
+                NOP_TRY(ctx->scratch("sn1d_tune_trace", sizeof(unsigned long long) * 3 * (size_t)B, &tp));
+                unsigned long long* tr_d = (unsigned long long*)tp;
+                Sn1dArgs ca = a;
+                ca.eigen = 0;
+                ca.itmax = 3;
+                ca.itmax_inner = 3;
+                ca.tol = ca.tol_inner = 0.0;
+                ca.trace = tr_d;
+                std::map<long long, std::array<std::vector<double>, 4>> meas;
+                std::vector<unsigned long long> tr(3 * (size_t)B);
+                std::vector<int> it_h(B);
+                for (int cand = 0; cand < 4; ++cand) {
+                    // 0: direct warp, 1: chunked warp, 2: direct team, 3: chunked team
+                    const bool direct = cand == 0 || cand == 2, team_c = cand >= 2;
+                    if (direct && !direct_ok) continue;
+                    std::vector<int> list, cfgv(B, 0);
+                    int smc = 1;
+                    for (auto& kv : todo)
+                        for (int b : kv.second) {
+                            if (cand == 3 && !fits_team(b)) continue;
+                            list.push_back(b);
+                            cfgv[b] = direct ? (SN1D_DIRECT | direct_A(b)) : chunked_cfg(b, team_c, nullptr);
+                            if (cand == 3) smc = std::max(smc, s.ncell[b]);
+                        }
+                    if (list.empty()) continue;
+                    if (team_c)
+                        NOP_TRY(launch(ca, {}, list, std::min<int>(blocks_max, (int)list.size()), cfgv, smc));
+                    else
+                        NOP_TRY(launch(ca, list, {}, 0, cfgv, smc));
+                    NOP_CUDA_TRY(ctx, cudaMemcpyAsync(tr.data(), tr_d, sizeof(unsigned long long) * 3 * B,
+                                                      cudaMemcpyDeviceToHost, ctx->stream));
+                    NOP_CUDA_TRY(ctx, cudaMemcpyAsync(it_h.data(), it_d, sizeof(int) * B,
+                                                      cudaMemcpyDeviceToHost, ctx->stream));
+                    NOP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+                    for (int b : list) {
+                        const double us = (double)(tr[3 * b + 1] - tr[3 * b]) * 1e-3;
+                        if (it_h[b] > 0 && us > 0)
+                            meas[key_of(b)][cand].push_back(us / it_h[b] / s.ncell[b]);
+                    }
+                }
+                for (auto& kv : meas) {
+                    std::array<double, 4> c4 = {-1.0, -1.0, -1.0, -1.0};
+                    for (int cand = 0; cand < 4; ++cand) {
+                        auto& v = kv.second[cand];
+                        if (v.empty()) continue;
+                        std::nth_element(v.begin(), v.begin() + v.size() / 2, v.end());
+                        c4[cand] = v[v.size() / 2];
+                    }
+                    table[kv.first] = c4;
+                }
+                // the calibration iterated on the solve's own arrays: start over
+                NOP_TRY(prepare());
+                ctx->last_tune_ms = std::chrono::duration<double, std::milli>(
+                                        std::chrono::steady_clock::now() - t0).count();
+            }
+            for (int b = 0; b < B; ++b) {
+                auto it = table.find(key_of(b));
+                const double I = s.ncell[b];
+                double c4[4] = {-1, -1, -1, -1};
+                if (it != table.end())
+                    for (int q = 0; q < 4; ++q) c4[q] = it->second[q];
+                // warp: the faster of the measured layouts (chunked if none was)
+                const bool d_w = c4[0] > 0 && (c4[1] <= 0 || c4[0] < c4[1]);
+                cw[b] = d_w ? (SN1D_DIRECT | direct_A(b)) : chunked_cfg(b, false, nullptr);
+                lw[b] = its_est[b] * I * (d_w ? c4[0] : (c4[1] > 0 ? c4[1] : 1.0));
+                const bool d_t = c4[2] > 0 && (c4[3] <= 0 || c4[2] < c4[3]);
+                if (d_t || (c4[3] > 0 && fits_team(b))) {
+                    ct[b] = d_t ? (SN1D_DIRECT | direct_A(b)) : chunked_cfg(b, true, nullptr);
+                    lt[b] = its_est[b] * I * (d_t ? c4[2] : c4[3]);
+                }
+            }
+        } else {
+            // ---- analytic model, in issue slots of one lane per source
+            // iteration (batches too small to measure, or NOP_SCHED_MODEL):
+            //   direct lanes on one warp: I steps of (12 + 14 A) slots plus about
+            //     80 per block of 32 cells; on a team two passes over a chunk of
+            //     ceil(I / 12) cells plus the team's barriers;
+            //   chunked lanes: both direction halves of sn1d_pick_config's model;
+            //   the correction: 4 passes over ceil((I + 1) / 32) edges.
+            // Direct lanes where at least 12 half-angles fill 3/4 of a half-warp.
+            auto dsa_slots = [&](int b) { return dsa ? 120.0 * ((s.ncell[b] + 32) / 32) * G : 0.0; };
+            for (int b = 0; b < B; ++b) {
+                const int I = s.ncell[b];
+                if (direct_ok && s.order[b] / 2 >= 12) {
+                    const int A = direct_A(b);
+                    cw[b] = ct[b] = SN1D_DIRECT | A;
+                    lw[b] = its_est[b] * G * (I * (12.0 + 14.0 * A) + 80.0 * ((I + 31) / 32));
+                    const double m = (double)((I + NW - 1) / NW);
+                    lt[b] = its_est[b] * G *
+                            (2.0 * m * (12.0 + 14.0 * A) + 160.0 * ((m + 31) / 32) + 3000.0);
+                } else {
+                    double half;
+                    cw[b] = chunked_cfg(b, false, &half);
+                    lw[b] = its_est[b] * (G * 2.0 * half + dsa_slots(b));
+                    if (fits_team(b)) {
+                        ct[b] = chunked_cfg(b, true, &half);
+                        lt[b] = its_est[b] * (G * 2.0 * half + dsa_slots(b));
+                    }
+                }
+            }
+        }
+        // Which instances get a team: with longest-first queues the batch takes
+        // about max(expected span, longest latency).  An instance whose one-warp
+        // latency is above the expected span S = (warp latencies + 12 x team
+        // latencies) / warps gets a team (a team costs more SM time than one
+        // warp, so only the instances that would outlast the batch are worth
+        // it); S is found by a few fixed-point rounds from the mean warp load.
+        std::vector<char> team;
+        double span = 0.0;
+        NOP_TRY(sn1d_select_teams(B, lw.data(), lt.data(), warps_total, NW,
+                                  o->schedule == NOP_SCHED_BLOCK ? 1 : (o->schedule == NOP_SCHED_WARP || B < 2 ? 2 : 0),
+                                  team, &span));
+        cfg.assign(B, 0);
+        std::vector<double> cost(B);
+        double big_work = 0, small_work = 0;
+        int n_direct = 0;
+        for (int b = 0; b < B; ++b) {
+            if (team[b]) {
+                cfg[b] = ct[b];
+                if (!(cfg[b] & SN1D_DIRECT)) smem_cells = std::max(smem_cells, s.ncell[b]);
+                big.push_back(b);
+                cost[b] = lt[b];
+                big_work += lt[b];
+            } else {
+                cfg[b] = cw[b];
+                small.push_back(b);
+                cost[b] = lw[b];
+                small_work += lw[b] / NW;
+            }
+            n_direct += (cfg[b] & SN1D_DIRECT) ? 1 : 0;
+        }
+        ctx->last_direct = n_direct;
+        // Large and small instances run side by side from the start: a share of
+        // the blocks proportional to the large instances' block-time takes the
+        // large queue first, the other blocks go straight to the small queue.
+        if (!big.empty()) {
+            const double share = big_work / std::max(1e-30, big_work + small_work);
+            big_blocks = (int)std::ceil(share * blocks_max);
+            big_blocks = std::max(1, std::min<int>(big_blocks, (int)big.size()));
+            if (small.empty()) big_blocks = std::min<int>(blocks_max, (int)big.size());
+        }
+        auto longest_first = [&](int x, int y) { return cost[x] > cost[y]; };
+        std::stable_sort(small.begin(), small.end(), longest_first);
+        std::stable_sort(big.begin(), big.end(), longest_first);
+        s.plan_cfg = cfg;
+        s.plan_small = small;
+        s.plan_big = big;
+        s.plan_big_blocks = big_blocks;
+        s.plan_smem_cells = smem_cells;
+        s.plan_direct = n_direct;
+        // the tuner may have added buckets: key the plan on the table as used
+        s.plan_key = plan_key();
+    }
+    for (int b = 0; b < B; ++b) k0_h[b] = (k0 && k0[b] > 0) ? k0[b] : 1.0;
+    NOP_CUDA_TRY(ctx, cudaMemcpyAsync(k0_d, k0_h, sizeof(double) * B,
+                                      cudaMemcpyHostToDevice, ctx->stream));
     mk = ctx->phase_begin(0);
-    sn1d_kernel<T><<<blocks, SN1D_THREADS, smem, ctx->stream>>>(a);
-    NOP_CUDA_TRY(ctx, cudaGetLastError());
+    NOP_TRY(launch(a, small, big, big_blocks, cfg, smem_cells));
     ctx->phase_end(mk);
-    ctx->count_launch(true);
     if (phi_out) {
         double* dst = phi_out;
         if (!out_dev) {

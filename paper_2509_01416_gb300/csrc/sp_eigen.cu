@@ -266,7 +266,11 @@ int sp_eigen(nop_ctx* ctx, double tol, int itmax, double* phi_d, std::vector<dou
     const nop_no_config& c = ctx->no.cfg;
     const bool fno = c.kind == NOP_NO_FNO1D || c.kind == NOP_NO_FNO2D;
     int* active_h = nullptr;
-    NOP_CUDA_TRY(ctx, cudaMallocHost(&active_h, sizeof(int)));
+    {
+        void* ph;
+        NOP_TRY(ctx->pinned("sp_active", sizeof(int), &ph));
+        active_h = (int*)ph;
+    }
     int rc = NOP_OK;
     const int mk = ctx->phase_begin(1);
     for (int it = 1; it <= itmax && rc == NOP_OK; ++it) {
@@ -323,7 +327,6 @@ int sp_eigen(nop_ctx* ctx, double tol, int itmax, double* phi_d, std::vector<dou
         }
         if (*active_h == 0) break;
     }
-    cudaFreeHost(active_h);
     if (rc != NOP_OK) {
         if (ctx->err.empty()) ctx->set_error("eigen warm start failed");
         return rc;

@@ -295,3 +295,67 @@ def test_anisotropic_rejected_outside_fixed_source_slabs(solver):
     with pytest.raises(NopError):
         solver.set_slabs(n, wdt, order, sigt, sigs, nu_sigma_f=0.5 * sigt, chi=[1.0],
                          sigma_s1=s.sigs1)
+
+
+# ------------------------------------------------------------ lane layouts
+def _direct_batch(seed=70):
+    """Vacuum slabs whose orders take the direct lanes (N >= 24): cell counts
+    from 1 to 5000 (ragged ring blocks of 32, chunks of 12 warps shorter than
+    one block), orders up to 128 (4 angles per lane)."""
+    rng = np.random.default_rng(seed)
+    shapes = [(1, 24), (31, 32), (32, 40), (33, 64), (97, 26), (300, 128), (2047, 48),
+              (5000, 30), (11, 64), (640, 56)]
+    return [W.slab_instance(np.random.default_rng(int(rng.integers(1 << 30))), I, N)
+            for I, N in shapes]
+
+
+@pytest.mark.parametrize("schedule", [1, 2])
+def test_direct_lanes_fp64_iterate_for_iterate(solver, schedule):
+    """One warp per instance (schedule 1) and a 12-warp team per instance
+    (schedule 2, chunk maps handed across warps): every source iterate equals
+    the oracle's to rounding, so the iteration counts agree too."""
+    insts = _direct_batch()
+    _set(solver, insts)
+    phi, info = solver.solve_fixed_source(tol=1e-9, itmax=100000, precision=1,
+                                          schedule=schedule)
+    for b, (s, ph) in enumerate(zip(insts, split(phi, insts))):
+        r = T.source_iteration(oracle_slab(s), Qd.gauss_legendre(s.N), tol=1e-9, itmax=100000)
+        assert abs(int(info["iterations"][b]) - r.iterations) <= 1, (s.I, s.N)
+        assert rel_l2(ph, r.phi[0]) < 1e-10, (s.I, s.N)
+
+
+def test_direct_and_chunked_layouts_agree_fp32(solver):
+    """The same FP32 batch on the direct lanes and on the chunked lanes: both
+    meet the workload bar against the oracle under the same stopping rule."""
+    insts = _direct_batch(71)
+    _set(solver, insts)
+    d, di = solver.solve_fixed_source(tol=1e-6, itmax=100000, precision=0)
+    c, ci = solver.solve_fixed_source(tol=1e-6, itmax=100000, precision=0, chunked=True)
+    for b, (s, pd, pc) in enumerate(zip(insts, split(d, insts), split(c, insts))):
+        r = T.source_iteration(oracle_slab(s), Qd.gauss_legendre(s.N), tol=1e-6, itmax=100000)
+        assert rel_l2(pd, r.phi[0]) <= 1e-5, (s.I, s.N)
+        assert rel_l2(pc, r.phi[0]) <= 1e-5, (s.I, s.N)
+        assert abs(int(di["iterations"][b]) - r.iterations) <= 1, (s.I, s.N)
+
+
+@pytest.mark.parametrize("schedule", [1, 2])
+def test_direct_lanes_multigroup_eigen_fp64(solver, schedule):
+    """Two groups with up- and down-scatter, power iteration, on the direct
+    lanes (S32, vacuum) against the oracle."""
+    rng = np.random.default_rng(72)
+    I, G = 150, 2
+    sigt = rng.uniform(0.8, 1.6, (G, I))
+    S = np.zeros((G, G, I))
+    S[0, 0], S[0, 1] = 0.4 * sigt[0], 0.2 * sigt[0]
+    S[1, 1], S[1, 0] = 0.6 * sigt[1], 0.1 * sigt[1]
+    nsf = np.stack([0.05 * np.ones(I), 0.3 * np.ones(I)])
+    chi = np.array([0.9, 0.1])
+    solver.set_slabs([I], [8.0], [32], sigt.reshape(-1), S.reshape(-1),
+                     nu_sigma_f=nsf.reshape(-1), chi=chi)
+    k, phi, info = solver.solve_eigen(tol=1e-10, tol_k=1e-12, tol_inner=1e-12, itmax=5000,
+                                      precision=1, schedule=schedule)
+    P = T.Slab(dx=np.full(I, 8.0 / I), sigt=sigt, sigs=S, nusigf=nsf, chi=chi)
+    e = T.power_iteration(P, Qd.gauss_legendre(32), tol_k=1e-13, tol_phi=1e-11,
+                          tol_inner=1e-13)
+    assert abs(k[0] - e.k) < 1e-9
+    assert rel_l2(phi, e.phi.reshape(-1)) < 1e-8
