@@ -85,6 +85,13 @@ extern "C" {
                               flux is unchanged.  NOP_EINVAL with sigma_s1 or
                               the x-y geometry.                               */
 
+#define NOP_GAUSS_SEIDEL 64 /* x-y: Gauss-Seidel over groups with the newest
+                              fluxes and quadrants in the order (-,-); (+,-)
+                              and (-,+); (+,+) with the newest reflected flux
+                              (the reference iteration).  Default: Jacobi in
+                              energy with the reflected inflow of the previous
+                              iteration, every group and quadrant swept in one
+                              launch; same fixed point, other iterates.       */
 #define NOP_SWEEP_CHUNKED 16 /* slabs: keep the chunked lane layout (angles x cell
                               chunks with a warp scan of the chunk maps) even
                               where the direct layout applies (vacuum faces,

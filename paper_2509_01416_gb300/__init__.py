@@ -82,8 +82,10 @@ __all__ = ["Solver", "NopError", "capi", "no_write_file", "no_read_file"]
 
 def _opts(tol=1e-6, itmax=10000, precision=NOP_PREC_F32, tol_k=1e-7, tol_inner=None,
           itmax_inner=10000, warm_start=NOP_WARM_NONE, recast_tol=1e-4, recast_itmax=200,
-          flags=0, schedule=0, dsa=False, chunked=False, cold=False):
+          flags=0, schedule=0, dsa=False, chunked=False, cold=False, gauss_seidel=False):
     o = capi.nop_solve_opts()
+    if gauss_seidel:
+        flags |= capi.NOP_GAUSS_SEIDEL
     if cold:
         flags |= capi.NOP_COLD_SCHEDULE
     if dsa:

@@ -20,6 +20,7 @@ NOP_PREC_F32, NOP_PREC_F64 = 0, 1
 NOP_WARM_NONE, NOP_WARM_RECAST, NOP_WARM_RECAST_CP = 0, 1, 2
 NOP_PHI0_DEVICE, NOP_OUT_DEVICE, NOP_SP_CONSTRAINED, NOP_DSA = 1, 2, 4, 8
 NOP_SWEEP_CHUNKED = 16
+NOP_GAUSS_SEIDEL = 64
 NOP_COLD_SCHEDULE = 32
 NOP_SCHED_AUTO, NOP_SCHED_WARP, NOP_SCHED_BLOCK, NOP_SCHED_MODEL = 0, 1, 2, 3
 NOP_SCHED_TUNE_MIN = 256

@@ -180,7 +180,9 @@ int refine_once(nop_ctx* ctx, const double* u, const double* src, double* out) {
     o.tol = 1e-300;
     o.itmax = 1;
     o.precision = NOP_PREC_F32;
-    o.flags = NOP_PHI0_DEVICE | NOP_OUT_DEVICE;
+    // one model source iteration of the reference order (Gauss-Seidel over
+    // groups), as Eq. A7-A8 apply it
+    o.flags = NOP_PHI0_DEVICE | NOP_OUT_DEVICE | NOP_GAUSS_SEIDEL;
     double* keep_src = ctx->src_d;
     ctx->src_d = const_cast<double*>(src);
     std::vector<int> keep_iters = ctx->slab.last_iters;

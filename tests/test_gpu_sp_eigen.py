@@ -256,8 +256,8 @@ def test_checkerboard_full_size_fno2d_warm_start(solver):
     assert np.all(np.isfinite(hist)) and hist[-10:].mean() < hist[:10].mean()
     solver.set_xy(c.nx, c.ny, c.Lx, c.Ly, c.sigt.reshape(-1), c.sigs.reshape(-1),
                   nu_sigma_f=c.nusigf.reshape(-1), chi=c.chi, bc=bc)
-    # stopping at a 2e-7 change keeps the truncation error below the bars
-    kw = dict(tol=2e-7, tol_k=1e-9, tol_inner=2e-7, itmax=2000, itmax_inner=400,
+    # stopping at a 1e-7 change keeps the truncation error below the bars
+    kw = dict(tol=1e-7, tol_k=1e-10, tol_inner=1e-7, itmax=2000, itmax_inner=120,
               allow_noconv=True)
     kp, php, ip = solver.solve_eigen(**kw)
     t3 = time.perf_counter()
