@@ -465,6 +465,30 @@ typedef struct {
                                 costs (0 when every bucket was known)          */
 } nop_timings;
 
+/* ----------------------------------------------------- diffusion batches */
+
+/* A second PDE on the recast driver (Sec. 3.1, Table 1): a batch of n_inst
+ * independent 1D slabs with -(D u')' + Sigma_a u = S on (0, width) and u = 0
+ * at both faces.  Table 1's diffusion row is Sigma_a = 0 with parameter
+ * p = D(x); its Helmholtz row -u'' - k^2 u = S is D = 1, Sigma_a = -k^2.
+ * Discretisation: n_cells uniform cells per instance, cell-centred finite
+ * volumes, face coefficients the harmonic mean of the two cells' D, a
+ * boundary face half a cell from its centre.  diffusion (> 0), absorption
+ * (finite; NULL = 0) and source are cell values of all instances
+ * concatenated (host, FP64, copied).  After this call nop_recast_iterate and
+ * nop_no_predict apply a DeepONet to the batch (its configuration's
+ * sigma_t_star and sigma_s_star are read as D* and Sigma_a*; the mismatch
+ * -dL = -(L(p) - L(p*)) of the discrete operators on the operator's grid is
+ * the recast source term), nop_diffusion_solve gives the model-based
+ * solution; the transport solves return NOP_ESTATE.  A later
+ * nop_set_problem replaces the batch. */
+int nop_set_diffusion(nop_ctx *ctx, int n_inst, const int *n_cells, const double *width,
+                      const double *diffusion, const double *absorption, const double *source);
+
+/* The model-based solution of the diffusion batch: every instance's
+ * tridiagonal system solved by elimination in FP64; u_out: host, C doubles. */
+int nop_diffusion_solve(nop_ctx *ctx, double *u_out);
+
 /* Measured arithmetic ceilings of the sweep (a microbenchmark, not the
  * paper's method): the device's rate of the special-function reciprocal
  * rcp.approx.ftz.f32 (one per diamond-difference cell-angle update) and of

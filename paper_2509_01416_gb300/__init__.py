@@ -283,6 +283,24 @@ class Solver:
         self._check(self._L.nop_set_problem(self.h, C.byref(p)), "nop_set_problem")
         self.n_inst, self.G, self.C = len(n_cells), G, int(n_cells.sum())
 
+    def set_diffusion(self, n_cells, width, diffusion, source, absorption=None):
+        """Batch of 1D diffusion slabs (Table 1): -(D u')' + Sigma_a u = S, u = 0
+        at the faces; cell arrays concatenated over the instances."""
+        n_cells = np.ascontiguousarray(n_cells, dtype=np.int32)
+        width = capi._f64(width)
+        d, s = capi._f64(diffusion), capi._f64(source)
+        a = None if absorption is None else capi._f64(absorption)
+        self._check(self._L.nop_set_diffusion(self.h, len(n_cells), capi._ptr(n_cells, capi._ip),
+                                              capi._ptr(width), capi._ptr(d), capi._ptr(a),
+                                              capi._ptr(s)), "nop_set_diffusion")
+        self.n_inst, self.G, self.C = len(n_cells), 1, int(n_cells.sum())
+
+    def diffusion_solve(self):
+        """The model-based solution of the diffusion batch (FP64)."""
+        out = np.zeros(self.C)
+        self._check(self._L.nop_diffusion_solve(self.h, capi._ptr(out)), "nop_diffusion_solve")
+        return out
+
     def set_xy(self, nx, ny, lx, ly, sigma_t, sigma_s, source=None, nu_sigma_f=None,
                chi=None, bc=(0, 0, 0, 0)):
         G = int(np.asarray(sigma_t).size // (nx * ny))

@@ -94,6 +94,8 @@ SIGNATURES = {
                                          C.c_void_p, C.POINTER(nop_stats)]),
     "nop_set_timing": (C.c_int, [C.c_void_p, C.c_int]),
     "nop_set_wait_limit": (C.c_int, [C.c_void_p, C.c_longlong]),
+    "nop_set_diffusion": (C.c_int, [C.c_void_p, C.c_int, _ip, _dp, _dp, _dp, _dp]),
+    "nop_diffusion_solve": (C.c_int, [C.c_void_p, _dp]),
     "nop_measure_alu_peaks": (C.c_int, [C.c_void_p, C.POINTER(C.c_double),
                                         C.POINTER(C.c_double)]),
     "nop_sched_select_teams": (C.c_int, [C.c_int, _dp, _dp, C.c_int, C.c_int, C.c_int, _ip,

@@ -318,6 +318,7 @@ int nop_set_problem(nop_ctx* ctx, const nop_problem* p) {
     if (!ctx || !p) return NOP_EINVAL;
     NOP_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
     ctx->has_problem = false;
+    ctx->diffusion = false;
     const int G = p->n_groups;
     if (G < 1 || G > 64) {
         ctx->set_error("n_groups must be in 1..64");
@@ -538,6 +539,10 @@ static int check_opts(nop_ctx* ctx, const nop_solve_opts* o, bool eigen) {
 int nop_solve_fixed_source(nop_ctx* ctx, const nop_solve_opts* o, const double* phi0,
                            double* phi_out, nop_stats* st) {
     if (!ctx) return NOP_EINVAL;
+    if (ctx->diffusion) {
+        ctx->set_error("a diffusion batch is solved by nop_diffusion_solve");
+        return NOP_ESTATE;
+    }
     ctx->phase_depth = 0;
     NOP_TRY(check_opts(ctx, o, false));
     if (!ctx->has_problem || !ctx->has_source) {

@@ -214,17 +214,29 @@ __global__ void project_kernel(int B, int M, const long long* cell_off, const in
     out[e] = (float)(acc / h);
 }
 
+// recast source of bin m: PS + PD u_m (+ PL u_{m-1} + PU u_{m+1} with the
+// off-diagonal mismatch bands of a diffusion batch)
+__device__ __forceinline__ float recast_src(const float* PS, const float* PD, const float* PL,
+                                            const float* PU, const float* u, long long e, int m,
+                                            int M) {
+    float s = PS[e] + PD[e] * u[e];
+    if (PL && m > 0) s += PL[e] * u[e - 1];
+    if (PU && m < M - 1) s += PU[e] * u[e + 1];
+    return s;
+}
+
 // Split and scale the bin sources of every instance (one block per instance):
-// src = PS + PD * u;  sigma+- = h sum max(+-src, 0);  rows 2b / 2b+1 of U are
-// src+/sigma+ and src-/sigma- (each part at unit integral, as in training).
-__global__ void split_kernel(int M, double h, const float* PS, const float* PD, const float* u,
-                             float* U, float* sig, int* flags) {
+// src = PS + PD * u (+ off-diagonal terms);  sigma+- = h sum max(+-src, 0);
+// rows 2b / 2b+1 of U are src+/sigma+ and src-/sigma- (each part at unit
+// integral, as in training).
+__global__ void split_kernel(int M, double h, const float* PS, const float* PD, const float* PL,
+                             const float* PU, const float* u, float* U, float* sig, int* flags) {
     __shared__ double red[2][32];
     const int b = blockIdx.x;
     // FP32 partial sums per thread, FP64 across threads
     float apf = 0.f, anf = 0.f;
     for (int m = threadIdx.x; m < M; m += blockDim.x) {
-        const float s = PS[(long long)b * M + m] + PD[(long long)b * M + m] * u[(long long)b * M + m];
+        const float s = recast_src(PS, PD, PL, PU, u, (long long)b * M + m, m, M);
         if (s > 0.f) apf += s;
         else anf -= s;
     }
@@ -247,7 +259,7 @@ __global__ void split_kernel(int M, double h, const float* PS, const float* PD, 
     sn *= h;
     const float ip = sp > 0 ? (float)(1.0 / sp) : 0.f, in = sn > 0 ? (float)(1.0 / sn) : 0.f;
     for (int m = threadIdx.x; m < M; m += blockDim.x) {
-        const float s = PS[(long long)b * M + m] + PD[(long long)b * M + m] * u[(long long)b * M + m];
+        const float s = recast_src(PS, PD, PL, PU, u, (long long)b * M + m, m, M);
         U[(2LL * b) * M + m] = fmaxf(s, 0.f) * ip;
         U[(2LL * b + 1) * M + m] = fmaxf(-s, 0.f) * in;
     }
@@ -470,6 +482,13 @@ int deeponet_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* sta
     float* PS = (float*)q;
     NOP_TRY(ctx->scratch("rc_PD", sizeof(float) * (size_t)B * M, &q));
     float* PD = (float*)q;
+    // off-diagonal bands of the mismatch (diffusion batches; null for transport)
+    float *PL = nullptr, *PU = nullptr;
+    if (ctx->diffusion) {
+        NOP_TRY(ctx->scratch("rc_PLU", sizeof(float) * 2 * (size_t)B * M, &q));
+        PL = (float*)q;
+        PU = PL + (size_t)B * M;
+    }
     NOP_TRY(ctx->scratch("rc_u", sizeof(float) * (size_t)B * M, &q));
     float* u = (float*)q;
     NOP_TRY(ctx->scratch("rc_unew", sizeof(float) * (size_t)B * M, &q));
@@ -501,13 +520,23 @@ int deeponet_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* sta
         B, M, s.cell_off_d, s.ncell_d, s.width_d, predict_only ? src_d : ctx->src_d,
         ctx->sigt_d, ctx->sigs_d, c.sigma_t_star, c.sigma_s_star, 0, PS);
     NOP_CUDA_TRY(ctx, cudaGetLastError());
-    project_kernel<<<(int)((BM_ + 255) / 256), 256, 0, ctx->stream>>>(
-        B, M, s.cell_off_d, s.ncell_d, s.width_d, nullptr, ctx->sigt_d, ctx->sigs_d,
-        c.sigma_t_star, c.sigma_s_star, 1, PD);
     NOP_CUDA_TRY(ctx, cudaGetLastError());
     ctx->count_launch(false);
-    ctx->count_launch(false);
-    if (predict_only) NOP_CUDA_TRY(ctx, cudaMemsetAsync(PD, 0, sizeof(float) * BM_, ctx->stream));
+    if (ctx->diffusion) {
+        // Table 1: -dL of -(D u')' + Sigma_a u on the bins; the operator's p*
+        // is (D*, Sigma_a*) = (sigma_t_star, sigma_s_star) of its configuration
+        NOP_TRY(diffusion_bands(ctx, M, c.sigma_t_star, c.sigma_s_star, PL, PD, PU));
+    } else {
+        project_kernel<<<(int)((BM_ + 255) / 256), 256, 0, ctx->stream>>>(
+            B, M, s.cell_off_d, s.ncell_d, s.width_d, nullptr, ctx->sigt_d, ctx->sigs_d,
+            c.sigma_t_star, c.sigma_s_star, 1, PD);
+        NOP_CUDA_TRY(ctx, cudaGetLastError());
+        ctx->count_launch(false);
+    }
+    if (predict_only) {
+        NOP_CUDA_TRY(ctx, cudaMemsetAsync(PD, 0, sizeof(float) * BM_, ctx->stream));
+        PL = PU = nullptr;
+    }
     NOP_CUDA_TRY(ctx, cudaMemsetAsync(u, 0, sizeof(float) * BM_, ctx->stream));
     NOP_CUDA_TRY(ctx, cudaMemsetAsync(flags, 0, sizeof(int) * (size_t)(4 * B + 4), ctx->stream));
     NOP_CUDA_TRY(ctx, cudaMemsetAsync(prev, 0x7f, sizeof(double) * (size_t)B, ctx->stream));
@@ -526,8 +555,8 @@ int deeponet_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* sta
     if (recast_fused_supported(c)) {
         const float* const Wl[4] = {Wp(ctx, 0, 0), Wp(ctx, 0, 1), Wp(ctx, 0, 2), Wp(ctx, 0, 3)};
         const float* const bl[4] = {Bp(ctx, 0, 0), Bp(ctx, 0, 1), Bp(ctx, 0, 2), Bp(ctx, 0, 3)};
-        rc = recast_fused_run(ctx, B, h, predict_only ? 1e300 : tol, imax, PS, PD, u, Wl, bl,
-                              Tref, beta, beta_keep, status, iters, prev, run, active, &it);
+        rc = recast_fused_run(ctx, B, h, predict_only ? 1e300 : tol, imax, PS, PD, PL, PU, u, Wl,
+                              bl, Tref, beta, beta_keep, status, iters, prev, run, active, &it);
         if (rc != NOP_OK) return rc;
         it = imax + 1;   // skip the generic loop
     }
@@ -535,7 +564,7 @@ int deeponet_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* sta
     NOP_TRY(ctx->pinned("rc_active", sizeof(int), &q));
     active_h = (int*)q;
     for (it = it == 0 ? 1 : it; it <= imax; ++it) {
-        split_kernel<<<B, 128, 0, ctx->stream>>>(M, h, PS, PD, u, Usp, sig, flags);
+        split_kernel<<<B, 128, 0, ctx->stream>>>(M, h, PS, PD, PL, PU, u, Usp, sig, flags);
         if (cudaGetLastError() != cudaSuccess) { rc = NOP_ECUDA; break; }
         ctx->count_launch(false);
         float* Bn;
@@ -702,7 +731,7 @@ int deeponet_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* sta
 // Steps of the recast iteration shared with the FNO (operator grid of M points).
 int recast_split(nop_ctx* ctx, int B, int M, double h, const float* PS, const float* PD,
                  const float* u, float* U, float* sig, int* flags) {
-    split_kernel<<<B, 128, 0, ctx->stream>>>(M, h, PS, PD, u, U, sig, flags);
+    split_kernel<<<B, 128, 0, ctx->stream>>>(M, h, PS, PD, nullptr, nullptr, u, U, sig, flags);
     NOP_CUDA_TRY(ctx, cudaGetLastError());
     ctx->count_launch(false);
     return NOP_OK;

@@ -430,6 +430,10 @@ namespace nop {
 // address comes back in *stat_h, valid once the stream is synchronised.
 int recast_enqueue(nop_ctx* ctx, double tol, int itmax, double* pd, const int** stat_h) {
     const int B = ctx->geometry == NOP_GEOM_SLAB ? ctx->slab.n_inst : 1;
+    if (ctx->diffusion && is_fno(ctx)) {
+        ctx->set_error("the diffusion recast runs with a DeepONet operator");
+        return NOP_EINVAL;
+    }
     void* p;
     NOP_TRY(ctx->scratch("rc_stat", sizeof(int) * 2 * B, &p));
     int* sd = (int*)p;

@@ -101,6 +101,7 @@ struct nop_ctx {
 
     // problem
     bool has_problem = false;
+    bool diffusion = false;   // a diffusion batch (nop_set_diffusion), not transport
     int geometry = 0;
     int G = 0;
     bool has_source = false, has_fission = false;
@@ -187,6 +188,10 @@ int deeponet_forward_raw(nop_ctx* ctx, int n, const float* U, int P, const float
 int deeponet_backward(nop_ctx* ctx, int n, int P, const float* dout, const float* U,
                       const float* X);
 int deeponet_project(nop_ctx* ctx, const double* field_host, float* out_host);
+// Recast mismatch bands of a diffusion batch on the operator's M-bin grid
+// (diffusion.cu): PL, PD, PU of -dL.
+int diffusion_bands(nop_ctx* ctx, int M, double d_star, double siga_star, float* PL, float* PD,
+                    float* PU);
 // The recast iteration (Eq. 24) enqueued without synchronising (no_capi.cu):
 // statistics land in a pinned buffer *stat_h, read by recast_collect after the
 // stream was synchronised.
@@ -221,7 +226,8 @@ int sp_eigen(nop_ctx* ctx, double tol, int itmax, double* phi_d, std::vector<dou
 // (recast_fused.cu); active2 points at two device counters.
 bool recast_fused_supported(const nop_no_config& c);
 int recast_fused_run(nop_ctx* ctx, int B, double h, double tol, int itmax, const float* PS,
-                     const float* PD, float* u, const float* const W[4], const float* const b[4],
+                     const float* PD, const float* PL, const float* PU, float* u,
+                     const float* const W[4], const float* const b[4],
                      const float* Tref, float* beta, float* beta_keep, int* status, int* iters,
                      double* prev, int* run, int* active2, int* its);
 

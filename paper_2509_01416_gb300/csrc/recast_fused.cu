@@ -33,6 +33,8 @@ struct RfArgs {
     int diverge_run;
     const float* PS;
     const float* PD;
+    const float* PL;            // off-diagonal mismatch bands (diffusion), or null
+    const float* PU;
     float* u;
     const __nv_bfloat16* Wbf;   // [5][128][128]: branch layers 1-4 ([out][in]), T_ref ([m][k])
     const float* bias[4];
@@ -140,7 +142,12 @@ __global__ void __launch_bounds__(RF_THREADS, 1) recast_fused_kernel(RfArgs a) {
             for (int j = 0; j < 4; ++j) {
                 const int m = lane + 32 * j;
                 const long long e = (long long)b * RF_W + m;
-                s[j] = b < a.B ? a.PS[e] + a.PD[e] * a.u[e] : 0.f;
+                s[j] = 0.f;
+                if (b < a.B) {
+                    s[j] = a.PS[e] + a.PD[e] * a.u[e];
+                    if (a.PL && m > 0) s[j] += a.PL[e] * a.u[e - 1];
+                    if (a.PU && m < RF_W - 1) s[j] += a.PU[e] * a.u[e + 1];
+                }
                 if (s[j] > 0.f) ap += s[j];
                 else an -= s[j];
             }
@@ -260,7 +267,8 @@ bool recast_fused_supported(const nop_no_config& c) {
 // The recast loop on the fused kernel (one launch).  active2: unused device
 // counters kept for the generic path's signature.  *its: the iteration cap.
 int recast_fused_run(nop_ctx* ctx, int B, double h, double tol, int itmax, const float* PS,
-                     const float* PD, float* u, const float* const W[4], const float* const b[4],
+                     const float* PD, const float* PL, const float* PU, float* u,
+                     const float* const W[4], const float* const b[4],
                      const float* Tref, float* beta, float* beta_keep, int* status, int* iters,
                      double* prev, int* run, int* active2, int* its) {
     void* p;
@@ -283,6 +291,8 @@ int recast_fused_run(nop_ctx* ctx, int B, double h, double tol, int itmax, const
     a.diverge_run = 5;
     a.PS = PS;
     a.PD = PD;
+    a.PL = PL;
+    a.PU = PU;
     a.u = u;
     a.Wbf = Wbf;
     for (int l = 0; l < 4; ++l) a.bias[l] = b[l];

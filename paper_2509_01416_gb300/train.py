@@ -26,6 +26,22 @@ def deeponet_training_set(solver, cfg, sources, order=32, tol=1e-7, itmax=100000
     return U, X, phi.reshape(n, I), info
 
 
+def diffusion_training_set(solver, cfg, sources):
+    """The diffusion batch at p* = (D*, Sigma_a*) = (cfg.sigma_t_star,
+    cfg.sigma_s_star) for every source row (n x I cells over cfg.length),
+    solved by nop_diffusion_solve (Table 1's recast takes its operator from
+    one parameter setting).  Returns (branch inputs [n, sensors], trunk
+    coordinates [I], targets [n, I])."""
+    n, I = sources.shape
+    solver.set_diffusion(np.full(n, I), np.full(n, cfg.length),
+                         np.full(n * I, cfg.sigma_t_star), sources.reshape(-1),
+                         absorption=np.full(n * I, cfg.sigma_s_star))
+    u = solver.diffusion_solve()
+    U = solver.no_sensors(sources.reshape(-1))
+    X = (np.arange(I) + 0.5) / I
+    return U, X, u.reshape(n, I)
+
+
 def fno1d_training_set(solver, cfg, sources, order=32, tol=1e-7, itmax=100000):
     """Solve the p* slab for every source row (n x I cells over cfg.length).
 

@@ -199,6 +199,26 @@ def aniso_slab(seed=25, I=100, N=32, sigt=1.2, sigs0=0.8, sigs1=0.3):
                   sigs1=sigs1 * one)
 
 
+D_STAR = (1.0, 0.0)            # (D*, Sigma_a*) of the diffusion operator
+
+
+def diffusion_slab(rng, I, L=L_SLAB, helmholtz=False):
+    """One diffusion slab of the recast's second PDE (Table 1): diffusion row,
+    D(x) = 1 + a sin(2 pi k x / L + ph) (a ~ U[0.2, 0.6], k ~ U{1..4}) with
+    Sigma_a = 0, or (helmholtz) the Helmholtz row, D = 1 with
+    Sigma_a = -k^2(x) = -(0.02 + 0.03 U[0,1]) below the first Dirichlet mode;
+    source a clipped Fourier series.  Returns (D, Sigma_a, S) on I cells."""
+    x = cell_centres(I, L)
+    if helmholtz:
+        D = np.ones(I)
+        siga = -(0.02 + 0.03 * rng.uniform(0, 1, I))
+    else:
+        a, k, ph = rng.uniform(0.2, 0.6), rng.integers(1, 5), rng.uniform(0, 2 * np.pi)
+        D = 1.0 + a * np.sin(2 * np.pi * k * x / L + ph)
+        siga = np.zeros(I)
+    return D, siga, fourier_source(rng, x, L)
+
+
 def slab_instance(rng, I, N):
     """One instance of the slab batch: sinusoidal or piecewise coefficients, Fourier Q."""
     x = cell_centres(I)
