@@ -114,6 +114,199 @@ def oracle_rate(insts, seconds, seed=0, pool=None):
     return done / el if el > 0 else 0.0, cores, done, el
 
 
+# ----------------------------------------------------- per-config lines
+def _events_ms(torch, stream, fn, reps=3):
+    """Median CUDA-event time (ms) of fn() on `stream` over reps runs after one warm-up."""
+    fn()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts)), out
+
+
+def run_configs(s, stream, deeponet_params, local):
+    """The four single-problem workloads on the GPU: plain guess and neural-
+    operator warm start, time to tolerance (CUDA events), iterations.  Each
+    operator is the workload's own, trained untimed at p* on solutions the
+    solver produces.  Returns (results, raw answers for the oracle leg)."""
+    import torch
+    from paper_2509_01416_gb300 import NOP_NO_FNO1D, NOP_NO_FNO2D, NOP_NO_DEEPONET, no_config
+    from paper_2509_01416_gb300 import train as TR
+    res, raw = {}, {}
+    clk = Clocks(local, os.path.join(ROOT, ".bench_clocks_configs.csv"))
+    clk.__enter__()
+    # ---- 1: uniform slab, S16, plain method, FP64 to a 1e-8 change
+    c = W.uniform_slab_s16()
+    s.set_slabs([c.I], [c.L], [c.N], c.sigt, c.sigs, source=c.Q)
+    clk.mark(True)
+    ms, (phi, info) = _events_ms(torch, stream, lambda: s.solve_fixed_source(
+        tol=1e-8, itmax=100000, precision=1))
+    res["1_uniform_slab_s16"] = {"plain": {"ms": ms, "iterations": int(info["iterations"][0])},
+                                 "precision": "f64", "tol": 1e-8}
+    raw["1"] = phi
+    # ---- 2: heterogeneous slab, S32, DeepONet warm start (the batch's operator)
+    c = W.hetero_slab_s32()
+    cfg2 = no_config(NOP_NO_DEEPONET, sensors=128, width=128, basis=128, depth=4,
+                     sigma_t_star=W.P_STAR[0], sigma_s_star=W.P_STAR[1], length=W.L_SLAB)
+    s.no_set(cfg2, deeponet_params)
+    s.set_slabs([c.I], [c.L], [c.N], c.sigt, c.sigs, source=c.Q)
+    kw = dict(tol=1e-6, itmax=100000, precision=0)
+    mp_, (pp, ip) = _events_ms(torch, stream, lambda: s.solve_fixed_source(**kw))
+    mw, (pw, iw) = _events_ms(torch, stream, lambda: s.solve_fixed_source(
+        warm_start=1, recast_tol=RECAST_TOL, recast_itmax=RECAST_ITMAX, **kw))
+    res["2_hetero_slab_s32"] = {
+        "plain": {"ms": mp_, "iterations": int(ip["iterations"][0])},
+        "warm": {"ms": mw, "iterations": int(iw["iterations"][0]),
+                 "recast_iterations": int(iw["recast_iterations"])},
+        "operator": "DeepONet 128 sensors, 4x128, p=128 (the batch's, trained above)",
+        "precision": "f32 sweeps, f64 norms", "tol": 1e-6}
+    raw["2"] = (pp, pw)
+    # ---- 3: three-region eigen slab, S32, FNO-1D (width 64, 32 modes) warm start
+    c = W.eigen_slab_s32()
+    nsf = c.nusigf.copy()
+    s.set_slabs([c.I], [c.L], [c.N], c.sigt, c.sigs, nu_sigma_f=nsf, chi=[1.0])
+    k0, _, _ = s.solve_eigen(tol=1e-7, tol_k=1e-9, tol_inner=1e-7, itmax=5000, precision=0,
+                             allow_noconv=True)
+    nsf = nsf * (c.k_target / k0[0])      # production scaled so that k is the recipe's target
+    cfg3 = no_config(NOP_NO_FNO1D, width=64, modes=32, depth=4, proj=128, length=W.L_SLAB)
+    s.no_set(cfg3, W.fno1d_init(31, width=64, modes=32, proj=128))
+    t0 = time.perf_counter()
+    S3, Y3, _ = TR.fno1d_training_set(s, cfg3, W.training_sources(32, 400, c.I))
+    h3 = TR.train_fno(s, S3, Y3, steps=800, batch=20, seed=33, lr=2e-3)
+    tr3 = time.perf_counter() - t0
+    s.set_slabs([c.I], [c.L], [c.N], c.sigt, c.sigs, nu_sigma_f=nsf, chi=[1.0])
+    kw = dict(tol=1e-6, tol_k=1e-7, tol_inner=1e-6, itmax=5000, itmax_inner=5000, precision=0)
+    mp_, (kp, pp, ip) = _events_ms(torch, stream, lambda: s.solve_eigen(**kw))
+    mw, (kwv, pw, iw) = _events_ms(torch, stream, lambda: s.solve_eigen(
+        warm_start=1, recast_tol=1e-3, recast_itmax=50, **kw))
+    res["3_eigen_slab_s32"] = {
+        "plain": {"ms": mp_, "inner": int(ip["inner"][0]), "outer": int(ip["outer"]),
+                  "k": float(kp[0])},
+        "warm": {"ms": mw, "inner": int(iw["inner"][0]), "outer": int(iw["outer"]),
+                 "k": float(kwv[0]), "recast_iterations": int(iw["recast_iterations"])},
+        "operator": "FNO-1D width 64, 32 modes, 4 layers (simple preconditioning, App. A2)",
+        "training": {"samples": 400, "steps": 800, "seconds": tr3,
+                     "loss_first": float(h3[0]), "loss_last": float(np.mean(h3[-20:]))},
+        "k_target": c.k_target, "precision": "f32 sweeps, f64 norms and k",
+        "tol": {"flux": 1e-6, "k": 1e-7}}
+    raw["3"] = (nsf, kp[0], pp, kwv[0], pw)
+    # ---- 4: 256x256 8-group checkerboard, LS S8, FNO-2D warm start
+    c = W.checkerboard_xy_8g()
+    bc = tuple(c.bc[f] for f in ("x0", "xL", "y0", "yL"))
+    cfg4 = no_config(NOP_NO_FNO2D, width=32, modes=16, depth=4, proj=128, length=c.Lx)
+    s.no_set(cfg4, W.fno2d_init(4, width=32, modes=16, proj=128))
+    t0 = time.perf_counter()
+    S4, Y4 = TR.fno2d_training_set(s, cfg4, W.training_sources_2d(6, 8, c.nx), bc=bc)
+    h4 = TR.train_fno(s, S4, Y4, steps=60, batch=2, seed=2, lr=2e-3)
+    tr4 = time.perf_counter() - t0
+    s.set_xy(c.nx, c.ny, c.Lx, c.Ly, c.sigt.reshape(-1), c.sigs.reshape(-1),
+             nu_sigma_f=c.nusigf.reshape(-1), chi=c.chi, bc=bc)
+    kw = dict(tol=1e-7, tol_k=1e-10, tol_inner=1e-7, itmax=2000, itmax_inner=120, precision=0,
+              allow_noconv=True)
+    mp_, (kp, pp, ip) = _events_ms(torch, stream, lambda: s.solve_eigen(**kw), reps=2)
+    mw, (kwv, pw, iw) = _events_ms(torch, stream, lambda: s.solve_eigen(
+        warm_start=1, recast_tol=1e-2, recast_itmax=10, **kw), reps=2)
+    clk.mark(False)
+    clk.__exit__()
+    res["4_checkerboard_xy_8g"] = {
+        "plain": {"ms": mp_, "inner": int(ip["inner"][0]), "outer": int(ip["outer"]),
+                  "k": float(kp[0])},
+        "warm": {"ms": mw, "inner": int(iw["inner"][0]), "outer": int(iw["outer"]),
+                 "k": float(kwv[0]), "recast_iterations": int(iw["recast_iterations"])},
+        "operator": "FNO-2D width 32, 16x16 modes, 4 layers (simple preconditioning)",
+        "training": {"samples": 8, "steps": 60, "seconds": tr4,
+                     "loss_first": float(h4[0]), "loss_last": float(np.mean(h4[-10:]))},
+        "precision": "f32 sweeps, f64 norms and k", "iteration": "Jacobi in energy (default)",
+        "tol": {"flux": 1e-7, "k": 1e-10}}
+    raw["4"] = (kp[0], pp, kwv[0], pw)
+    return res, raw, clk.summary()
+
+
+def _oracle_config(job):
+    """One config's FP64 oracle, single thread: (seconds, result)."""
+    from oracle import quadrature as Qd
+    from oracle import transport as T
+    kind = job[0]
+    t0 = time.perf_counter()
+    if kind == "fixed":
+        _, I, L, N, sigt, sigs, Q, tol = job
+        r = T.source_iteration(T.uniform_slab(I, L, sigt, sigs, Q=Q), Qd.gauss_legendre(N),
+                               tol=tol, itmax=1000000)
+        out = (r.phi[0], r.iterations)
+    elif kind == "eigen":
+        _, I, L, N, sigt, sigs, nsf, tk, tp, ti = job
+        e = T.power_iteration(T.uniform_slab(I, L, sigt, sigs, nusigf=nsf), Qd.gauss_legendre(N),
+                              tol_k=tk, tol_phi=tp, tol_inner=ti)
+        out = (e.phi[0], e.k, e.outer, e.inner_total)
+    else:   # a bounded sample of the x-y oracle: two source iterations of config 4
+        c = W.checkerboard_xy_8g()
+        bcm = {k: (T.REFLECTIVE if v else T.VACUUM) for k, v in c.bc.items()}
+        P = T.XY(dx=c.Lx / c.nx, dy=c.Ly / c.ny, sigt=c.sigt, sigs=c.sigs, nusigf=c.nusigf,
+                 chi=c.chi, bc=bcm)
+        T.source_iteration(P, Qd.level_symmetric_s8(), src=np.zeros_like(c.sigt),
+                           phi0=np.ones_like(c.sigt), tol=0.0, itmax=2)
+        out = None
+    return time.perf_counter() - t0, out
+
+
+def oracle_configs(res, raw, pool):
+    """The oracle beside every config (single thread each, in parallel over
+    configs): its time and iterations, and the GPU answers' errors against it."""
+    from tests.helpers import rel_l2, xy_golden
+    c1, c2, c3 = W.uniform_slab_s16(), W.hetero_slab_s32(), W.eigen_slab_s32()
+    nsf3 = raw["3"][0]
+    jobs = {
+        "1": ("fixed", c1.I, c1.L, c1.N, c1.sigt, c1.sigs, c1.Q, 1e-8),
+        "2": ("fixed", c2.I, c2.L, c2.N, c2.sigt, c2.sigs, c2.Q, 1e-6),
+        "2c": ("fixed", c2.I, c2.L, c2.N, c2.sigt, c2.sigs, c2.Q, 1e-12),
+        "3": ("eigen", c3.I, c3.L, c3.N, c3.sigt, c3.sigs, nsf3, 1e-7, 1e-6, 1e-6),
+        "3c": ("eigen", c3.I, c3.L, c3.N, c3.sigt, c3.sigs, nsf3, 1e-12, 1e-10, 1e-12),
+        "4": ("xy_sample",),
+    }
+    fut = {k: pool.apply_async(_oracle_config, (j,)) for k, j in jobs.items()}
+    out = {k: f.get() for k, f in fut.items()}
+    t1, (o1, it1) = out["1"]
+    res["1_uniform_slab_s16"]["oracle"] = {"seconds": t1, "iterations": it1, "threads": 1}
+    res["1_uniform_slab_s16"]["error_vs_oracle"] = {"flux_rel_l2_same_rule": rel_l2(raw["1"], o1)}
+    t2, (o2, it2) = out["2"]
+    _, (o2c, _) = out["2c"]
+    pp, pw = raw["2"]
+    res["2_hetero_slab_s32"]["oracle"] = {"seconds": t2, "iterations": it2, "threads": 1}
+    res["2_hetero_slab_s32"]["error_vs_oracle"] = {
+        "plain_flux_rel_l2_same_rule": rel_l2(pp, o2), "warm_flux_rel_l2_same_rule": rel_l2(pw, o2),
+        "warm_flux_rel_l2_vs_converged": rel_l2(pw, o2c)}
+    t3, (o3, k3, n3, in3) = out["3"]
+    _, (o3c, k3c, _, _) = out["3c"]
+    _, kp, pp, kw_, pw = raw["3"]
+    res["3_eigen_slab_s32"]["oracle"] = {"seconds": t3, "outer": n3, "inner": in3, "k": k3,
+                                         "threads": 1}
+    res["3_eigen_slab_s32"]["error_vs_oracle"] = {
+        "plain_dk_same_rule": abs(kp - k3), "warm_dk_same_rule": abs(kw_ - k3),
+        "plain_flux_rel_l2_same_rule": rel_l2(pp, o3), "warm_flux_rel_l2_same_rule": rel_l2(pw, o3),
+        "warm_dk_vs_converged": abs(kw_ - k3c), "warm_flux_rel_l2_vs_converged": rel_l2(pw, o3c)}
+    t4, _ = out["4"]
+    k0, g, j, i, ref, _ = xy_golden()
+    c4 = W.checkerboard_xy_8g()
+    kp, pp, kw_, pw = raw["4"]
+    res["4_checkerboard_xy_8g"]["oracle"] = {
+        "seconds_per_source_iteration": t4 / 2, "threads": 1,
+        "seconds_to_converge_estimate": t4 / 2 * 918,
+        "note": "a timed sample of 2 source iterations; the converged oracle solve "
+                "(tests/golden/make_xy_golden.py) takes 918 inner iterations"}
+    res["4_checkerboard_xy_8g"]["error_vs_oracle"] = {
+        "plain_dk": abs(kp - k0), "warm_dk": abs(kw_ - k0),
+        "plain_flux_rel_l2_sampled": rel_l2(pp.reshape(c4.sigt.shape)[g, j, i], ref),
+        "warm_flux_rel_l2_sampled": rel_l2(pw.reshape(c4.sigt.shape)[g, j, i], ref),
+        "against": "converged FP64 oracle (tests/golden/xy_checkerboard_8g.txt)"}
+    return res
+
+
 # ---------------------------------------------------------------- clocks
 class Clocks:
     """nvidia-smi sampler (every 50 ms).  It starts before the plain-guess
@@ -213,6 +406,8 @@ def main():
                     help="profiling aid: time a fixed amount of x-y sweep work instead")
     ap.add_argument("--no-dsa", action="store_true",
                     help="skip the diffusion-synthetic-acceleration comparison runs")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the four single-problem workloads (per-config lines)")
     ap.add_argument("--instances", type=int, default=0,
                     help="solve only the first N instances of the batch (profiling aid)")
     args = ap.parse_args()
@@ -363,6 +558,11 @@ def main():
     e2e_s = time.perf_counter() - t0
     e2e_value = whole_job_rate(world, B, args.steps, max_over_ranks(e2e_s, world, "cuda"))
 
+    # ---- the four single-problem workloads beside the batch (rank 0, N=1)
+    configs = cfg_raw = cfg_clk = None
+    if rank == 0 and world == 1 and not args.no_configs:
+        configs, cfg_raw, cfg_clk = run_configs(s, stream, s.no_get(), local)
+
     if rank != 0:
         s.close()
         if world > 1:
@@ -388,6 +588,8 @@ def main():
 
     cpu = None
     if pool is not None:
+        if configs is not None:
+            configs = oracle_configs(configs, cfg_raw, pool)
         rate, cores_used, nsol, el = oracle_rate(insts, args.cpu_seconds, pool=pool)
         pool.terminate()
         pool.join()
@@ -459,6 +661,7 @@ def main():
                      "sweep_algorithmic_gbs": sweep_gbs,
                      "sweep_algorithmic_frac_of_hbm": sweep_gbs / float(peaks.get("hbm_gbs", 6800.0))},
         "cpu_baseline": cpu,
+        "configs": None if configs is None else dict(configs, clocks=cfg_clk),
     }
     print(json.dumps(line))
     s.close()

@@ -144,7 +144,7 @@ __global__ void check_kernel(long long nt, const double* sigt, long long ns, con
 // about 30% rms, where the largest local ratio overestimates them 14-fold.)
 __global__ void rho_kernel(int G, long long C, const long long* cell_off, const int* ncell,
                            const double* width, const double* sigt, const double* sigs,
-                           double* rho) {
+                           double* rho, double* siga_mean) {
     __shared__ double red[2][32];
     const int b = blockIdx.x;
     double best = 0.0;
@@ -174,6 +174,7 @@ __global__ void rho_kernel(int G, long long C, const long long* cell_off, const 
             const double Bg = M_PI / (width[b] + 2.0 * 0.7104 / stm);
             const double D = 1.0 / (3.0 * stm);
             const double r = (st > 0 ? ss / st : 0.0) / (1.0 + D * Bg * Bg / stm);
+            if (r > best || g == 0) siga_mean[b] = (st - ss) / ncell[b];
             best = fmax(best, r);
         }
         __syncthreads();
@@ -466,13 +467,16 @@ int nop_set_problem(nop_ctx* ctx, const nop_problem* p) {
         s.width_d = (double*)d;
         NOP_TRY(upload(ctx, "boff", boff.data(), sizeof(long long) * B, &d));
         s.boff_d = (long long*)d;
-        NOP_TRY(ctx->scratch("rho", sizeof(double) * B, &d));
+        NOP_TRY(ctx->scratch("rho", sizeof(double) * 2 * B, &d));
         double* rho_d = (double*)d;
         rho_kernel<<<B, 128, 0, ctx->stream>>>(G, C, s.cell_off_d, s.ncell_d, s.width_d,
-                                               ctx->sigt_d, ctx->sigs_d, rho_d);
+                                               ctx->sigt_d, ctx->sigs_d, rho_d, rho_d + B);
         NOP_CUDA_TRY(ctx, cudaGetLastError());
         s.rho.assign(B, 0.0);
+        s.siga_mean.assign(B, 0.0);
         NOP_CUDA_TRY(ctx, cudaMemcpyAsync(s.rho.data(), rho_d, sizeof(double) * B,
+                                          cudaMemcpyDeviceToHost, ctx->stream));
+        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(s.siga_mean.data(), rho_d + B, sizeof(double) * B,
                                           cudaMemcpyDeviceToHost, ctx->stream));
         NOP_TRY(nop::build_gauss_legendre(ctx));   // synchronises the stream
     } else {

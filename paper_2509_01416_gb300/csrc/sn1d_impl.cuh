@@ -1603,12 +1603,27 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
     // with and without the diffusion correction (they differ several times)
     std::vector<int>& last = dsa ? s.last_iters_dsa : s.last_iters;
     const bool cold = (o->flags & NOP_COLD_SCHEDULE) != 0;
+    // a slab solve seeded by the DeepONet/FNO recast prediction
+    const bool warm_recast = !eigen && o->warm_start == NOP_WARM_RECAST && phi0 != nullptr &&
+                             ctx->no.loaded;
     std::vector<double> its_est(B);
     for (int b = 0; b < B; ++b) {
         const double c = std::min(0.9999, std::max(0.05, s.rho[b]));
         double its = std::min(5000.0, std::max(5.0, 1.3 * std::log(tol_its) / std::log(c)));
         // the accelerated iteration contracts like about c/4 (Fourier analysis)
         if (dsa) its = std::max(3.0, std::log(tol_its) / std::log(std::max(0.05, 0.25 * c)));
+        if (warm_recast && !dsa) {
+            // the recast warm start removes the part of the initial error its
+            // prediction gets right: after K recast steps, contracting like
+            // rho_rec = |Sigma_a / Sigma_a* - 1| (the mismatch relative to
+            // the operator's p*), the prediction is off by about
+            // e0 = max(0.02, rho_rec^K) of the zero guess's error, saving
+            // log(1 / e0) / log(1 / rho) source iterations
+            const double sa_star = ctx->no.cfg.sigma_t_star - ctx->no.cfg.sigma_s_star;
+            const double rr = sa_star > 0 ? std::fabs(s.siga_mean[b] / sa_star - 1.0) : 1.0;
+            const double e0 = std::max(0.02, std::pow(std::min(1.0, rr), (double)std::max(1, o->recast_itmax)));
+            its = std::max(3.0, its - std::log(1.0 / e0) / std::log(1.0 / c));
+        }
         if (!eigen && !cold && b < (int)last.size() && last[b] > 0) its = last[b];
         its_est[b] = its;
     }
@@ -1636,6 +1651,7 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
         mix(eigen ? 1 : 0);
         mix((unsigned long long)(o->flags & (NOP_DSA | NOP_SWEEP_CHUNKED | NOP_COLD_SCHEDULE)));
         mix((unsigned long long)o->schedule);
+        mix(warm_recast ? (unsigned long long)o->recast_itmax + 1 : 0ull);
         mix((unsigned long long)ctx->bc[0] * 2 + ctx->bc[1]);
         mix(p1 ? 1 : 0);
         double t = tol_its;
