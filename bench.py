@@ -37,7 +37,7 @@ RECAST_ITMAX = 10
 # DRAM bytes (read + write) of one warm-step sweep launch on this workload,
 # from the ncu capture summarised in profiles/sn1d_kernel_4096slab.txt; None
 # once the sweep kernel changes until it is captured again.
-SWEEP_TRAFFIC_BYTES = None
+SWEEP_TRAFFIC_BYTES = 70_464_256 + 54_725_888
 WORKLOAD = ("4096 slabs, cells U{64..2048}, GL S_N N even U{8..64}, sinusoidal or "
             "piecewise coefficients, Fourier sources, vacuum, tol 1e-6 rel. L2 flux change")
 
@@ -404,6 +404,9 @@ def main():
     ap.add_argument("--recast-itmax", type=int, default=RECAST_ITMAX)
     ap.add_argument("--xy-sweep", action="store_true",
                     help="profiling aid: time a fixed amount of x-y sweep work instead")
+    ap.add_argument("--slab-sweep", type=int, default=0, metavar="N",
+                    help="profiling aid: time the plain solve of the first N instances "
+                         "of the batch instead (cold, tuned schedule)")
     ap.add_argument("--no-dsa", action="store_true",
                     help="skip the diffusion-synthetic-acceleration comparison runs")
     ap.add_argument("--no-configs", action="store_true",
@@ -425,6 +428,9 @@ def main():
         return
     if args.xy_sweep:
         run_xy_sweep(local)
+        return
+    if args.slab_sweep > 0:
+        run_slab_sweep(local, args.slab_sweep)
         return
 
     # the oracle's process pool starts before the first GPU call
@@ -705,6 +711,40 @@ def run_xy_sweep(local):
                       "sweep_phase_ms": tm["sweep_ms"], "inner_iterations": inner,
                       "outer_iterations": int(info["outer"]), "launches": int(tm["launches"]),
                       "config": {"workload": "checkerboard_xy_8g: 256x256, 8 groups, LS S8"}}))
+    s.close()
+
+
+def run_slab_sweep(local, n):
+    """Profiling aid, not the headline: the plain FP32 solve (tol 1e-6, cold
+    schedule) of the first n instances of the batch, twice; the first solve
+    calibrates the measured schedule (four candidate sweep launches, then the
+    solve's own), so the sixth sn1d_kernel launch is the second solve's sweep,
+    timed here with CUDA events.  Prints one JSON line."""
+    import torch
+    from paper_2509_01416_gb300 import Solver
+    torch.cuda.set_device(local)
+    n_, wdt, order, sigt, sigs, src, _ = W.slab_batch_arrays(rank_instances(0, n))
+    stream = torch.cuda.Stream()
+    s = Solver(local)
+    s.set_stream(stream.cuda_stream)
+    s.set_slabs(n_, wdt, order, sigt, sigs, source=src)
+    phi = torch.empty(int(n_.sum()), dtype=torch.float64, device="cuda")
+    kw = dict(tol=TOL, itmax=200000, precision=0, cold=True)
+    s.solve_fixed_source_dev(phi.data_ptr(), **kw)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.set_timing(True)
+    ev0.record(stream)
+    info = s.solve_fixed_source_dev(phi.data_ptr(), **kw)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    tm = s.timing()
+    s.set_timing(False)
+    print(json.dumps({"metric": "slab cell-angle updates per second", "unit": "updates/s",
+                      "value": tm["cell_angle_updates"] / (tm["sweep_ms"] / 1e3),
+                      "solve_ms": ev0.elapsed_time(ev1), "sweep_ms": tm["sweep_ms"],
+                      "iterations": int(np.sum(info["iterations"])),
+                      "config": {"workload": "first %d instances of the 4096-slab batch" % n}}))
     s.close()
 
 
