@@ -207,7 +207,9 @@ def run_configs(s, stream, deeponet_params, local):
     tr4 = time.perf_counter() - t0
     s.set_xy(c.nx, c.ny, c.Lx, c.Ly, c.sigt.reshape(-1), c.sigs.reshape(-1),
              nu_sigma_f=c.nusigf.reshape(-1), chi=c.chi, bc=bc)
-    kw = dict(tol=1e-7, tol_k=1e-10, tol_inner=1e-7, itmax=2000, itmax_inner=120, precision=0,
+    # |dk|/k below about 1e-9 is under the noise of k from FP32 fluxes: the
+    # outer loop then stops only when the noise happens to fall below it
+    kw = dict(tol=1e-7, tol_k=1e-8, tol_inner=1e-7, itmax=2000, itmax_inner=120, precision=0,
               allow_noconv=True)
     mp_, (kp, pp, ip) = _events_ms(torch, stream, lambda: s.solve_eigen(**kw), reps=2)
     mw, (kwv, pw, iw) = _events_ms(torch, stream, lambda: s.solve_eigen(
@@ -223,7 +225,7 @@ def run_configs(s, stream, deeponet_params, local):
         "training": {"samples": 8, "steps": 60, "seconds": tr4,
                      "loss_first": float(h4[0]), "loss_last": float(np.mean(h4[-10:]))},
         "precision": "f32 sweeps, f64 norms and k", "iteration": "Jacobi in energy (default)",
-        "tol": {"flux": 1e-7, "k": 1e-10}}
+        "tol": {"flux": 1e-7, "k": 1e-8}}
     raw["4"] = (kp[0], pp, kwv[0], pw)
     return res, raw, clk.summary()
 

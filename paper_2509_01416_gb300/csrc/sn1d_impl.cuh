@@ -726,10 +726,109 @@ __device__ __forceinline__ void direct_stage(const DirectSmem<T>& sm, int buf, i
     p.s1 = vp.y * vp.phi + vp.z;
     m.s0 = vm.st;
     m.s1 = vm.y * vm.phi + vm.z;
+    if constexpr (sizeof(T) == 4) {
+        // FP32 stages {-2 sigma_t, 2 s} (exact scalings; see direct_steps_f32)
+        p.s0 *= T(-2);
+        p.s1 *= T(2);
+        m.s0 *= T(-2);
+        m.s1 *= T(2);
+    }
     sm.stg[(2 + buf) * (DR + 2) + l] = p;   // mu > 0 rows: 2, 3
     sm.stg[buf * (DR + 2) + l] = m;         // mu < 0 rows: 0, 1
     php = vp.phi;
     phm = vm.phi;
+}
+
+// ---- FP32 steps of the direct lanes.  The staged operands are scaled so
+// that each product the recurrence needs is one rounding of exactly twice the
+// unscaled value (scaling by 2 commutes with rounding): with S0 = -2 sigma_t
+// and S1 = 2 s,
+//     x = fma(S0, psi, S1) = 2 (s - sigma_t psi),   d = r x = 2 dl,
+//     psi_c = fma(1/2, d, psi) = psi + dl,          c + sigma_t = fma(-1/2, S0, c),
+// and the chunk map's D <- D + 2 r sigma_t (1 - D) is fma(r S0, D - 1, D).
+// Two angles of a lane go through one instruction as a packed pair
+// (__ffma2_rn, __fmul2_rn, __fadd2_rn: sm_100 and later); the compensated sum
+// of psi is the same Fast2Sum as CSum, on pairs.
+__device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
+
+__device__ __forceinline__ float2 rcp2(float2 d) {
+    float2 r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(d.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(d.y));
+    const float2 e = __ffma2_rn(make_float2(-d.x, -d.y), r, f2(1.0f));
+    return __ffma2_rn(r, e, r);
+}
+
+// P packed pairs of chains over the nk staged steps of `cur` (COMPOSE: chunk
+// maps; otherwise flux partial sums into myred[k]).  r0 holds the reciprocals
+// of step 0 on entry.
+template <int P, bool COMPOSE>
+__device__ __forceinline__ void direct_steps_f32x2(const Cell2<float>* cur, int nk, float* myred,
+                                                   const float2 (&c2)[P], const float2 (&w2)[P],
+                                                   float2 (&h2)[P], float2 (&l2)[P],
+                                                   float2 (&D2)[P], float2 (&r0)[P]) {
+    Cell2<float> v1 = cur[1];
+    float S0 = cur[0].s0, S1 = cur[0].s1;
+#pragma unroll 2
+    for (int k = 0; k < nk; ++k) {
+        float2 r[P];
+#pragma unroll
+        for (int j = 0; j < P; ++j) r[j] = r0[j];
+        const Cell2<float> v2 = cur[k + 2];
+#pragma unroll
+        for (int j = 0; j < P; ++j) r0[j] = rcp2(__ffma2_rn(f2(-0.5f), f2(v1.s0), c2[j]));
+        float2 pa = f2(0.0f);
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            const float2 x = __ffma2_rn(f2(S0), h2[j], f2(S1));
+            const float2 d = __fmul2_rn(r[j], x);
+            if constexpr (COMPOSE) {
+                const float2 g = __fmul2_rn(r[j], f2(S0));
+                D2[j] = __ffma2_rn(g, __fadd2_rn(D2[j], f2(-1.0f)), D2[j]);
+            } else {
+                const float2 pc = __ffma2_rn(f2(0.5f), d, h2[j]);
+                pa = j == 0 ? __fmul2_rn(w2[j], pc) : __ffma2_rn(w2[j], pc, pa);
+            }
+            const float2 u = __fadd2_rn(d, l2[j]);
+            const float2 t = __fadd2_rn(h2[j], u);
+            const float2 y = __ffma2_rn(h2[j], f2(-1.0f), t);   // t - psi (exact)
+            l2[j] = __ffma2_rn(y, f2(-1.0f), u);
+            h2[j] = t;
+        }
+        if constexpr (!COMPOSE) myred[k] = pa.x + pa.y;
+        S0 = v1.s0;
+        S1 = v1.s1;
+        v1 = v2;
+    }
+}
+
+// The same for one chain per lane (A = 1), unpacked.
+template <bool COMPOSE>
+__device__ __forceinline__ void direct_steps_f32(const Cell2<float>* cur, int nk, float* myred,
+                                                 float c, float w, float& h, float& l, float& D,
+                                                 float& r0) {
+    Cell2<float> v1 = cur[1];
+    float S0 = cur[0].s0, S1 = cur[0].s1;
+#pragma unroll 2
+    for (int k = 0; k < nk; ++k) {
+        const float r = r0;
+        const Cell2<float> v2 = cur[k + 2];
+        r0 = rcp_dd(fmaf(-0.5f, v1.s0, c));
+        const float x = fmaf(S0, h, S1);
+        const float d = r * x;
+        if constexpr (COMPOSE) {
+            D = fmaf(r * S0, D - 1.0f, D);
+        } else {
+            myred[k] = w * fmaf(0.5f, d, h);
+        }
+        const float u = d + l;
+        const float t = h + u;
+        l = u - (t - h);
+        h = t;
+        S0 = v1.s0;
+        S1 = v1.s1;
+        v1 = v2;
+    }
 }
 
 // One pass over this warp's chunk [c0, c0 + len) for all its chains.
@@ -751,6 +850,21 @@ __device__ __forceinline__ void direct_pass(const DirectSmem<T>& sm, Cell4<T>* X
     const int nblk = (len + DR - 1) / DR;
     const Cell2<T>* row = sm.stg + 2 * half * (DR + 2);
     T* myred = sm.red + lane * (DR + 1);
+    // FP32 with two or more chains per lane: packed pairs (an odd last chain
+    // is paired with an idle one: c = 1, w = 0)
+    constexpr int P2 = (A + 1) / 2;
+    float2 c2[P2], w2[P2], h2[P2], l2[P2], D2[P2];
+    if constexpr (sizeof(T) == 4 && A > 1) {
+#pragma unroll
+        for (int j = 0; j < P2; ++j) {
+            const int q = 2 * j, q1 = 2 * j + 1;
+            c2[j] = make_float2((float)cc[q], q1 < A ? (float)cc[q1] : 1.0f);
+            w2[j] = make_float2((float)wt[q], q1 < A ? (float)wt[q1] : 0.0f);
+            h2[j] = make_float2((float)psi[q].hi, q1 < A ? (float)psi[q1].hi : 0.0f);
+            l2[j] = make_float2((float)psi[q].lo, q1 < A ? (float)psi[q1].lo : 0.0f);
+            D2[j] = make_float2((float)D[q], q1 < A ? (float)D[q1] : 0.0f);
+        }
+    }
 #pragma unroll 1
     for (int kb = 0; kb < nblk; ++kb) {
         // the next block's cells, in flight during this block's steps
@@ -758,13 +872,25 @@ __device__ __forceinline__ void direct_pass(const DirectSmem<T>& sm, Cell4<T>* X
         const int nk = min(DR, len - kb * DR);
         const Cell2<T>* cur = row + (kb & 1) * (DR + 2);
         // two-deep pipeline: step k loads the operands of step k + 2 and
-        // forms the reciprocals of step k + 1 (slots DR, DR + 1 are padding)
+        // forms the reciprocals of step k + 1 (slots DR, DR + 1 are padding);
+        // two steps per loop trip, so the independent work of consecutive
+        // steps (operands, reciprocals, angle sums) interleaves with the
+        // flux chain
+        if constexpr (sizeof(T) == 4 && A == 1) {
+            float rr = rcp_dd(fmaf(-0.5f, cur[0].s0, cc[0]));
+            direct_steps_f32<COMPOSE>((const Cell2<float>*)cur, nk, (float*)myred, cc[0], wt[0],
+                                      psi[0].hi, psi[0].lo, D[0], rr);
+        } else if constexpr (sizeof(T) == 4) {
+            float2 rr[P2];
+#pragma unroll
+            for (int j = 0; j < P2; ++j) rr[j] = rcp2(__ffma2_rn(f2(-0.5f), f2(cur[0].s0), c2[j]));
+            direct_steps_f32x2<P2, COMPOSE>((const Cell2<float>*)cur, nk, (float*)myred, c2, w2,
+                                            h2, l2, D2, rr);
+        } else {
         Cell2<T> v0 = cur[0], v1 = cur[1];
         T r0[A];
 #pragma unroll
         for (int q = 0; q < A; ++q) r0[q] = rcp_dd(cc[q] + v0.s0);
-        // two steps per loop trip: the independent work of consecutive steps
-        // (operands, reciprocals, angle sums) interleaves with the flux chain
 #pragma unroll 2
         for (int k = 0; k < nk; ++k) {
             const T st = v0.s0, s = v0.s1;
@@ -793,6 +919,7 @@ __device__ __forceinline__ void direct_pass(const DirectSmem<T>& sm, Cell4<T>* X
                 }
                 myred[k] = p;
             }
+        }
         }
         __syncwarp();
         if constexpr (!COMPOSE) {
@@ -840,6 +967,20 @@ __device__ __forceinline__ void direct_pass(const DirectSmem<T>& sm, Cell4<T>* X
         }
         if (kb + 1 < nblk) direct_stage<T>(sm, (kb + 1) & 1, lane, vp, vm, php, phm);
         __syncwarp();
+    }
+    if constexpr (sizeof(T) == 4 && A > 1) {
+#pragma unroll
+        for (int j = 0; j < P2; ++j) {
+            const int q = 2 * j, q1 = 2 * j + 1;
+            psi[q].hi = h2[j].x;
+            psi[q].lo = l2[j].x;
+            D[q] = D2[j].x;
+            if (q1 < A) {
+                psi[q1].hi = h2[j].y;
+                psi[q1].lo = l2[j].y;
+                D[q1] = D2[j].y;
+            }
+        }
     }
 }
 
