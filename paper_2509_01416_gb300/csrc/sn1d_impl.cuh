@@ -1736,9 +1736,10 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
 
     // ---- scheduling (host side).  Estimated iterations of an instance: those
     // of the previous solve of the same batch layout when known (unless the
-    // caller asks for a cold schedule), else log(tol) / log(rho) with rho the
-    // estimated contraction of set-up (rho_kernel), scaled by 1.3 (the median
-    // ratio of measured to estimated counts on the 4096-slab batch).
+    // caller asks for a cold schedule), else 0.94 log(tol) / log(rho) with rho
+    // the diffusion estimate of the source iteration's spectral radius made at
+    // set-up (rho_si_kernel; 0.94 is the median ratio of measured to
+    // estimated counts on the 4096-slab batch).
     const double tol_its = eigen ? std::min(o->tol_inner, o->tol) : o->tol;
     // iterations of the previous solve of this layout, kept apart for solves
     // with and without the diffusion correction (they differ several times)
@@ -1750,7 +1751,8 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
     std::vector<double> its_est(B);
     for (int b = 0; b < B; ++b) {
         const double c = std::min(0.9999, std::max(0.05, s.rho[b]));
-        double its = std::min(5000.0, std::max(5.0, 1.3 * std::log(tol_its) / std::log(c)));
+        const double rs = std::min(0.9999, std::max(0.05, b < (int)s.rho_si.size() ? s.rho_si[b] : c));
+        double its = std::min(5000.0, std::max(5.0, 0.94 * std::log(tol_its) / std::log(rs)));
         // the accelerated iteration contracts like about c/4 (Fourier analysis)
         if (dsa) its = std::max(3.0, std::log(tol_its) / std::log(std::max(0.05, 0.25 * c)));
         if (warm_recast && !dsa) {
@@ -1763,7 +1765,7 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
             const double sa_star = ctx->no.cfg.sigma_t_star - ctx->no.cfg.sigma_s_star;
             const double rr = sa_star > 0 ? std::fabs(s.siga_mean[b] / sa_star - 1.0) : 1.0;
             const double e0 = std::max(0.02, std::pow(std::min(1.0, rr), (double)std::max(1, o->recast_itmax)));
-            its = std::max(3.0, its - std::log(1.0 / e0) / std::log(1.0 / c));
+            its = std::max(3.0, its - std::log(1.0 / e0) / std::log(1.0 / rs));
         }
         if (!eigen && !cold && b < (int)last.size() && last[b] > 0) its = last[b];
         its_est[b] = its;
