@@ -501,13 +501,18 @@ int nop_measure_alu_peaks(nop_ctx *ctx, double *rcp_per_s, double *fma_per_s);
 /* The slab batch scheduler's team selection, exported so that its logic can
  * be checked without a GPU (host arithmetic only).  lat_warp[b]: latency of
  * instance b on one warp; lat_team[b]: on a team of team_width warps (< 0:
- * no team).  mode 0: an instance gets a team when its warp latency exceeds
- * the expected span S = (warp latencies of the warp instances + team_width x
- * team latencies of the team instances) / warps, found by fixed-point rounds
- * from the mean warp load; mode 1: every instance that can; mode 2: none.
- * team_out[b] receives 0/1; *span_out (may be NULL) the final S. */
+ * no team).  mode 0: instances are taken in decreasing warp latency, and
+ * each gets a team while margin x its warp latency exceeds the expected span
+ * S = (warp latencies of the warp instances + team_width x team latencies of
+ * the team instances) / warps, S updated after every pick; margin >= 1 covers
+ * errors of the latency estimates (a team costs little extra SM time next to
+ * the whole batch, an instance left on a warp that outlasts S costs the whole
+ * difference); mode 1: every instance that can; mode 2: none.  team_out[b]
+ * receives 0/1; *span_out (may be NULL) the final S.  NOP_EINVAL for
+ * margin < 1, warps < 1 or team_width < 1. */
 int nop_sched_select_teams(int n, const double *lat_warp, const double *lat_team, int warps,
-                           int team_width, int mode, int *team_out, double *span_out);
+                           int team_width, int mode, double margin, int *team_out,
+                           double *span_out);
 
 /* Failure detection.  Every wait of a tensor-core kernel on its own products
  * (an mbarrier poll) is bounded; when the bound runs out the kernel records

@@ -98,7 +98,7 @@ SIGNATURES = {
     "nop_diffusion_solve": (C.c_int, [C.c_void_p, _dp]),
     "nop_measure_alu_peaks": (C.c_int, [C.c_void_p, C.POINTER(C.c_double),
                                         C.POINTER(C.c_double)]),
-    "nop_sched_select_teams": (C.c_int, [C.c_int, _dp, _dp, C.c_int, C.c_int, C.c_int, _ip,
+    "nop_sched_select_teams": (C.c_int, [C.c_int, _dp, _dp, C.c_int, C.c_int, C.c_int, C.c_double, _ip,
                                          C.POINTER(C.c_double)]),
     "nop_slab_solve_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                                          C.c_int, C.c_double, C.c_int, C.c_void_p, C.c_void_p,

@@ -188,96 +188,188 @@ __global__ void rho_kernel(int G, long long C, const long long* cell_off, const 
 // flux response to an isotropic source without scattering; its P1 form is
 // M = -(D u')' + Sigma_t with D = 1 / (3 Sigma_t) (harmonic face values, a
 // Marshak condition J = u / 2 at a vacuum face, J = 0 at a reflective one).
-// The radius is 1 / lambda_min of M v = lambda Sigma_s v, by inverse
-// iteration with (M - Sigma_s)^{-1} Sigma_s -- M - Sigma_s is the absorption
-// operator, symmetric and diagonally dominant, so its elimination is stable
-// -- and the Rayleigh quotient v'Mv / v'Sigma_s v.  One thread per instance
-// and group; `work` holds two doubles per cell and group (inverse pivots and
-// the iterate).  On the 4096-slab batch this predicts the iteration counts of
-// the plain source iteration to 4.6% rms (times a fitted 0.94), where the
-// mean scattering ratio times a leakage factor was off by 26% rms.
-__device__ __forceinline__ double fv_face(const double* st, int I, int i, double h, bool refl) {
-    if (i == 0 || i == I) {
-        if (refl) return 0.0;
-        const double D = 1.0 / (3.0 * st[i == 0 ? 0 : I - 1]);
-        return 2.0 * D / (h + 4.0 * D);
-    }
-    const double Dl = 1.0 / (3.0 * st[i - 1]), Dr = 1.0 / (3.0 * st[i]);
-    return 2.0 * Dl * Dr / (Dl + Dr) / h;
-}
-
-__global__ void rho_si_kernel(int B, int G, long long C, const long long* cell_off,
-                              const int* ncell, const double* width, const double* sigt,
-                              const double* sigs, int refl0, int reflL, double* work,
-                              double* rho) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= B * G) return;
+// With A = M - Sigma_s (the absorption operator) and mu the largest
+// eigenvalue of A^{-1} Sigma_s, M v = (1 + 1/mu) Sigma_s v, so the radius is
+// mu / (1 + mu).  mu comes from inverse iteration y = A^{-1} Sigma_s v with
+// the Rayleigh quotient v'Sigma_s y / v'Sigma_s v.  Every quantity stays
+// positive: A is a diagonally dominant M-matrix whose elimination pivots are
+// carried as p_k = t_k + |u_k|, t_k = a_k + |l_k| t_{k-1} / p_{k-1} (a_k the
+// row's excess over its off-diagonal sum: absorption and face leakage), and
+// the iterate of the fundamental mode is positive, so FP32 loses nothing to
+// cancellation.  One warp per instance and group, lane l owning a chunk of
+// ceil(I / 32) cells: each recurrence (the pivots, a Moebius map of
+// t_{k-1} / p_{k-1}; forward substitution; back substitution, affine maps) is
+// composed per chunk, the chunk maps are scanned across the lanes with
+// shuffles, and every lane then runs its chunk from its entry value.  `work`
+// holds six floats per cell and group.  On the 4096-slab batch this predicts
+// the iteration counts of plain source iteration to 4.6% rms (times a fitted
+// 0.94), where the mean scattering ratio times a leakage factor was off by
+// 26% rms.
+__global__ void __launch_bounds__(128) rho_si_kernel(int B, int G, long long C,
+                                                     const long long* cell_off, const int* ncell,
+                                                     const double* width, const double* sigt,
+                                                     const double* sigs, int refl0, int reflL,
+                                                     float* work, double* rho) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int e = blockIdx.x * 4 + (threadIdx.x >> 5);
+    if (e >= B * G) return;   // uniform over the warp
     const int b = e / G, g = e % G;
     const int I = ncell[b];
     const long long o = cell_off[b];
     const double h = width[b] / I;
     const double* st = sigt + (long long)g * C + o;
     const double* ss = sigs + ((long long)g * G + g) * C + o;
-    double* pinv = work + 2 * ((long long)g * C + o);
-    double* v = pinv + I;
-    // row i of A = M - Sigma_s: lo_i u_{i-1} + dg_i u_i + up_i u_{i+1}
-    auto row = [&](int i, double& lo, double& dg, double& up) {
-        const double fw = fv_face(st, I, i, h, refl0 != 0), fe = fv_face(st, I, i + 1, h, reflL != 0);
-        lo = -fw / h;
-        up = -fe / h;
-        dg = (fw + fe) / h + st[i] - ss[i];
+    float* ipv = work + 6 * ((long long)g * C + o);   // 1 / p_k
+    float* alf = ipv + I;                            // |l_k| / p_k
+    float* cup = alf + I;                            // |u_k| / p_k
+    float* ssf = cup + I;                            // Sigma_s
+    float* v = ssf + I;                              // iterate
+    float* z = v + I;                                // forward-substitution values
+    const int m = (I + 31) / 32;
+    const int k0 = min(I, lane * m), k1 = min(I, k0 + m);
+    // face coupling between cells i and i + 1 per unit volume, D_face / h^2
+    // with the harmonic D_face = 2 / (3 (sigma_t,i + sigma_t,i+1)); a vacuum
+    // face leaks (2D / (h + 4D)) / h
+    const float kf = (float)(2.0 / (3.0 * h * h));
+    auto leak = [&](double sg) {
+        const double D = 1.0 / (3.0 * sg);
+        return (float)(2.0 * D / ((h + 4.0 * D) * h));
     };
-    bool ok = true;
-    double cprev = 0.0;
-    for (int i = 0; i < I; ++i) {
-        double lo, dg, up;
-        row(i, lo, dg, up);
-        const double piv = dg - lo * cprev;
-        if (!(piv > 1e-300)) ok = false;
-        pinv[i] = ok ? 1.0 / piv : 0.0;
-        cprev = up * pinv[i];
-        v[i] = 1.0;
+    auto coef = [&](int k, float& lo, float& up, float& a, float& ssk) {
+        const float stk = (float)st[k];
+        ssk = (float)ss[k];
+        lo = k > 0 ? kf / ((float)st[k - 1] + stk) : 0.0f;
+        up = k < I - 1 ? kf / (stk + (float)st[k + 1]) : 0.0f;
+        a = fmaxf(stk - ssk, 0.0f);
+        if (k == 0 && !refl0) a += leak(st[0]);
+        if (k == I - 1 && !reflL) a += leak(st[I - 1]);
+    };
+    // ---- pivots: x_k = t_k / p_k = (|l| x + a) / (|l| x + a + |u|), x_{-1} = 0
+    float m00 = 1.0f, m01 = 0.0f, m10 = 0.0f, m11 = 1.0f;
+    auto mnorm = [&]() {
+        const float mx = fmaxf(fmaxf(m00, m01), fmaxf(m10, m11));
+        if (mx > 0.0f) {
+            const float r = 1.0f / mx;
+            m00 *= r;
+            m01 *= r;
+            m10 *= r;
+            m11 *= r;
+        }
+    };
+    for (int k = k0; k < k1; ++k) {
+        float lo, up, a, ssk;
+        coef(k, lo, up, a, ssk);
+        const float n00 = lo * m00 + a * m10, n01 = lo * m01 + a * m11;
+        const float n10 = lo * m00 + (a + up) * m10, n11 = lo * m01 + (a + up) * m11;
+        m00 = n00;
+        m01 = n01;
+        m10 = n10;
+        m11 = n11;
+        mnorm();
     }
-    double lam = 0.0;
-    for (int it = 0; ok && it < 8; ++it) {
-        // forward elimination of Sigma_s v, then back substitution
-        double zprev = 0.0;
-        for (int i = 0; i < I; ++i) {
-            double lo, dg, up;
-            row(i, lo, dg, up);
-            zprev = (ss[i] * v[i] - lo * zprev) * pinv[i];
-            v[i] = zprev;
+    for (int d = 1; d < 32; d <<= 1) {   // inclusive prefix: later chunks on the left
+        const float p00 = __shfl_up_sync(FULL, m00, d), p01 = __shfl_up_sync(FULL, m01, d);
+        const float p10 = __shfl_up_sync(FULL, m10, d), p11 = __shfl_up_sync(FULL, m11, d);
+        if (lane >= d) {
+            const float n00 = m00 * p00 + m01 * p10, n01 = m00 * p01 + m01 * p11;
+            const float n10 = m10 * p00 + m11 * p10, n11 = m10 * p01 + m11 * p11;
+            m00 = n00;
+            m01 = n01;
+            m10 = n10;
+            m11 = n11;
+            mnorm();
         }
-        double ynext = 0.0;
-        for (int i = I - 1; i >= 0; --i) {
-            double lo, dg, up;
-            row(i, lo, dg, up);
-            ynext = v[i] - up * pinv[i] * ynext;
-            v[i] = ynext;
+    }
+    {
+        const float q01 = __shfl_up_sync(FULL, m01, 1), q11 = __shfl_up_sync(FULL, m11, 1);
+        float x = (lane > 0 && q11 > 0.0f) ? q01 / q11 : 0.0f;
+        for (int k = k0; k < k1; ++k) {
+            float lo, up, a, ssk;
+            coef(k, lo, up, a, ssk);
+            const float t = a + lo * x;
+            const float p = t + up;
+            const float ip = p > 0.0f ? 1.0f / p : 0.0f;
+            ipv[k] = ip;
+            alf[k] = lo * ip;
+            cup[k] = up * ip;
+            ssf[k] = ssk;
+            v[k] = 1.0f;
+            x = t * ip;
         }
-        // Rayleigh quotient y'My / y'Sigma_s y, and rescaling
-        double num = 0.0, den = 0.0, mx = 0.0;
-        for (int i = 0; i < I; ++i) {
-            double lo, dg, up;
-            row(i, lo, dg, up);
-            const double Ay = dg * v[i] + (i > 0 ? lo * v[i - 1] : 0.0) +
-                              (i < I - 1 ? up * v[i + 1] : 0.0);
-            num += v[i] * (Ay + ss[i] * v[i]);
-            den += ss[i] * v[i] * v[i];
-            mx = fmax(mx, fabs(v[i]));
+    }
+    // ---- inverse iteration y = A^{-1} Sigma_s v and the Rayleigh quotient
+    double mu = 0.0;
+    float sc = 1.0f;
+    for (int it = 0; it < 5; ++it) {
+        // forward substitution z_k = alf_k z_{k-1} + Sigma_s v_k / p_k
+        float A = 1.0f, Bv = 0.0f;
+        for (int k = k0; k < k1; ++k) {
+            const float al = alf[k];
+            Bv = fmaf(al, Bv, ssf[k] * (v[k] * sc) * ipv[k]);
+            A *= al;
         }
+        for (int d = 1; d < 32; d <<= 1) {
+            const float pA = __shfl_up_sync(FULL, A, d), pB = __shfl_up_sync(FULL, Bv, d);
+            if (lane >= d) {
+                Bv = fmaf(A, pB, Bv);
+                A *= pA;
+            }
+        }
+        float zc = __shfl_up_sync(FULL, Bv, 1);
+        if (lane == 0) zc = 0.0f;
+        for (int k = k0; k < k1; ++k) {
+            zc = fmaf(alf[k], zc, ssf[k] * (v[k] * sc) * ipv[k]);
+            z[k] = zc;
+        }
+        __syncwarp();
+        // back substitution y_k = z_k + cup_k y_{k+1}, from the right
+        A = 1.0f;
+        Bv = 0.0f;
+        for (int k = k1 - 1; k >= k0; --k) {
+            const float c = cup[k];
+            Bv = fmaf(c, Bv, z[k]);
+            A *= c;
+        }
+        for (int d = 1; d < 32; d <<= 1) {
+            const float pA = __shfl_down_sync(FULL, A, d), pB = __shfl_down_sync(FULL, Bv, d);
+            if (lane + d < 32) {
+                Bv = fmaf(A, pB, Bv);
+                A *= pA;
+            }
+        }
+        float yc = __shfl_down_sync(FULL, Bv, 1);
+        if (lane == 31) yc = 0.0f;
+        double num = 0.0, den = 0.0;
+        float mx = 0.0f;
+        for (int k = k1 - 1; k >= k0; --k) {
+            yc = fmaf(cup[k], yc, z[k]);
+            const float vk = v[k] * sc;
+            const float sv = ssf[k] * vk;
+            num += (double)(sv * yc);
+            den += (double)(sv * vk);
+            v[k] = yc;
+            mx = fmaxf(mx, yc);
+        }
+        for (int d = 16; d > 0; d >>= 1) {
+            num += __shfl_xor_sync(FULL, num, d);
+            den += __shfl_xor_sync(FULL, den, d);
+            mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, d));
+        }
+        __syncwarp();
         if (!(den > 0.0) || !(mx > 0.0) || !isfinite(num)) {
-            ok = false;
+            mu = 0.0;
             break;
         }
-        lam = num / den;
-        const double sc = 1.0 / mx;
-        for (int i = 0; i < I; ++i) v[i] *= sc;
+        mu = num / den;
+        sc = 1.0f / mx;
     }
-    // no scattering: nothing to iterate; a singular absorption operator: the
-    // slowest possible iteration
-    const double r = ok ? (lam > 1.0 ? 1.0 / lam : 0.9999) : (lam == 0.0 ? 0.0 : 0.9999);
-    rho[e] = fmin(0.9999, fmax(0.0, r));
+    // no scattering: nothing to iterate; a singular absorption operator (no
+    // absorption, reflective faces): the slowest possible iteration
+    if (lane == 0) {
+        const double r = isfinite(mu) ? mu / (1.0 + mu) : 0.9999;
+        rho[e] = fmin(0.9999, fmax(0.0, r));
+    }
 }
 
 }  // namespace
@@ -345,11 +437,12 @@ int nop_set_stream(nop_ctx* ctx, void* stream) {
 }
 
 int nop_sched_select_teams(int n, const double* lat_warp, const double* lat_team, int warps,
-                           int team_width, int mode, int* team_out, double* span_out) {
+                           int team_width, int mode, double margin, int* team_out,
+                           double* span_out) {
     if (n < 0 || (n > 0 && !team_out) || mode < 0 || mode > 2) return NOP_EINVAL;
     std::vector<char> team;
-    const int rc = nop::sn1d_select_teams(n, lat_warp, lat_team, warps, team_width, mode, team,
-                                          span_out);
+    const int rc = nop::sn1d_select_teams(n, lat_warp, lat_team, warps, team_width, mode, margin,
+                                          team, span_out);
     if (rc != NOP_OK) return rc;
     for (int b = 0; b < n; ++b) team_out[b] = team[b];
     return NOP_OK;
@@ -576,11 +669,12 @@ int nop_set_problem(nop_ctx* ctx, const nop_problem* p) {
                                           cudaMemcpyDeviceToHost, ctx->stream));
         NOP_CUDA_TRY(ctx, cudaMemcpyAsync(s.siga_mean.data(), rho_d + B, sizeof(double) * B,
                                           cudaMemcpyDeviceToHost, ctx->stream));
-        NOP_TRY(ctx->scratch("rho_si", sizeof(double) * ((size_t)B * G + 2 * (size_t)G * C), &d));
+        NOP_TRY(ctx->scratch("rho_si", sizeof(double) * (size_t)B * G +
+                                           sizeof(float) * 6 * (size_t)G * C, &d));
         double* rsi_d = (double*)d;
-        rho_si_kernel<<<(B * G + 127) / 128, 128, 0, ctx->stream>>>(
+        rho_si_kernel<<<(B * G + 3) / 4, 128, 0, ctx->stream>>>(
             B, G, C, s.cell_off_d, s.ncell_d, s.width_d, ctx->sigt_d, ctx->sigs_d, ctx->bc[0],
-            ctx->bc[1], rsi_d + (size_t)B * G, rsi_d);
+            ctx->bc[1], (float*)(rsi_d + (size_t)B * G), rsi_d);
         NOP_CUDA_TRY(ctx, cudaGetLastError());
         std::vector<double> rsi((size_t)B * G);
         NOP_CUDA_TRY(ctx, cudaMemcpyAsync(rsi.data(), rsi_d, sizeof(double) * B * G,

@@ -251,7 +251,7 @@ int xy_solve(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
 // Lane split of the 1D sweep (log2 lanes per angle group, angles per lane).
 // team selection of the slab batch scheduler (sn1d.cu)
 int sn1d_select_teams(int n, const double* lat_w, const double* lat_t, int warps, int width,
-                      int mode, std::vector<char>& team, double* span);
+                      int mode, double margin, std::vector<char>& team, double* span);
 
 // lane split of the chunked layout for I cells and order N; cost_out: the
 // model's issue slots of one direction half per iteration

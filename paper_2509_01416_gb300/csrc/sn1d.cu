@@ -64,8 +64,9 @@ void sn1d_pick_config(int I, int N, int* lg_out, int* A_out, bool pow2, double* 
 // warp (that could have a team) outlasts S.  mode 1: every instance that can;
 // mode 2: none.  Returns the final S in *span.
 int sn1d_select_teams(int n, const double* lat_w, const double* lat_t, int warps, int width,
-                      int mode, std::vector<char>& team, double* span) {
-    if (n < 0 || warps < 1 || width < 1 || (n > 0 && (!lat_w || !lat_t))) return NOP_EINVAL;
+                      int mode, double margin, std::vector<char>& team, double* span) {
+    if (n < 0 || warps < 1 || width < 1 || !(margin >= 1.0) || (n > 0 && (!lat_w || !lat_t)))
+        return NOP_EINVAL;
     team.assign(n, 0);
     double work = 0.0;
     for (int b = 0; b < n; ++b) work += lat_w[b];
@@ -82,7 +83,7 @@ int sn1d_select_teams(int n, const double* lat_w, const double* lat_t, int warps
         std::stable_sort(cand.begin(), cand.end(),
                          [&](int x, int y) { return lat_w[x] > lat_w[y]; });
         for (int b : cand) {
-            if (!(lat_w[b] > work / warps)) break;
+            if (!(margin * lat_w[b] > work / warps)) break;
             team[b] = 1;
             work += width * lat_t[b] - lat_w[b];
         }

@@ -9,7 +9,7 @@ from paper_2509_01416_gb300 import build as B
 from paper_2509_01416_gb300 import capi
 
 
-def _select(lw, lt, warps, width=12, mode=0):
+def _select(lw, lt, warps, width=12, mode=0, margin=1.0):
     B.build()
     L = capi.lib()
     lw = np.ascontiguousarray(lw, dtype=np.float64)
@@ -17,7 +17,7 @@ def _select(lw, lt, warps, width=12, mode=0):
     team = np.zeros(len(lw), dtype=np.int32)
     span = C.c_double()
     rc = L.nop_sched_select_teams(len(lw), capi._ptr(lw), capi._ptr(lt), warps, width, mode,
-                                  capi._ptr(team, capi._ip), C.byref(span))
+                                  margin, capi._ptr(team, capi._ip), C.byref(span))
     assert rc == 0
     return team.astype(bool), span.value
 
@@ -63,3 +63,26 @@ def test_no_warp_instance_outlasts_the_span_and_teams_are_the_longest():
         assert np.all(lw[~team] <= span * (1 + 1e-12))
         if team.any():
             assert lw[team].min() >= lw[~team].max()
+
+
+def test_margin_leaves_no_warp_instance_near_the_span():
+    # with margin m, an instance stays on a warp only while m x its latency is
+    # within the span, so every warp instance ends by span / m
+    rng = np.random.default_rng(7)
+    for _ in range(10):
+        lw = rng.lognormal(0.0, 1.0, 500)
+        lt = lw / rng.uniform(3, 8, 500)
+        t1, s1 = _select(lw, lt, warps=150, margin=1.0)
+        t2, s2 = _select(lw, lt, warps=150, margin=1.25)
+        assert np.all(1.25 * lw[~t2] <= s2 * (1 + 1e-12))
+        assert t2.sum() >= t1.sum() and np.all(t2[t1])
+
+
+def test_margin_below_one_is_rejected():
+    B.build()
+    L = capi.lib()
+    lw = np.ones(3)
+    team = np.zeros(3, dtype=np.int32)
+    rc = L.nop_sched_select_teams(3, capi._ptr(lw), capi._ptr(lw), 3, 12, 0, 0.9,
+                                  capi._ptr(team, capi._ip), None)
+    assert rc != 0
