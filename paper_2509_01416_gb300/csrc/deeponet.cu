@@ -186,32 +186,43 @@ int mlp_backward(nop_ctx* ctx, int net, int rows, const float* X, const float* d
 }
 
 // ------------------------------------------------------------ recast kernels
-// Overlap-weighted bin average of a cell field: bins of width h = L/M, cells
-// of width dx = L/I of instance b.  f(c) is read through `mode`: 0 the field
-// itself, 1 the recast mismatch (Sigma_s - Sigma_s*) - (Sigma_t - Sigma_t*).
+// Overlap-weighted bin averages of cell fields: bins of width h = L/M, cells
+// of width dx = L/I of instance b, one thread per bin.  out0 receives the
+// average of `field` (when given), out1 (when given) that of the recast
+// mismatch (Sigma_s - Sigma_s*) - (Sigma_t - Sigma_t*), both from one pass
+// over the bin's cells.  The cell edges are taken relative to the bin's left
+// edge (found in FP64 once per bin), so the overlaps and sums run in FP32
+// without the rounding of positions far from the origin.
 __global__ void project_kernel(int B, int M, const long long* cell_off, const int* ncell,
                                const double* width, const double* field, const double* sigt,
-                               const double* sigs, double st_star, double ss_star, int mode,
-                               float* out) {
+                               const double* sigs, double st_star, double ss_star, float* out0,
+                               float* out1) {
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (e >= (long long)B * M) return;
     const int b = (int)(e / M), m = (int)(e % M);
     const int I = ncell[b];
     const double L = width[b], h = L / M, dx = L / I;
-    const double lo = m * h, hi = (m + 1) * h;
+    const double lo = m * h;
     int i0 = (int)floor(lo / dx);
-    int i1 = (int)floor(hi / dx);
+    int i1 = (int)floor((m + 1) * h / dx);
     i0 = max(0, min(I - 1, i0));
     i1 = max(0, min(I - 1, i1));
-    double acc = 0.0;
+    const float hf = (float)h, dxf = (float)dx;
+    const float left0 = (float)(i0 * dx - lo);   // edge of cell i0 from the bin's edge
+    const float sts = (float)st_star, sss = (float)ss_star;
+    const long long c0 = cell_off[b];
+    float a0 = 0.f, a1 = 0.f;
     for (int i = i0; i <= i1; ++i) {
-        const double ov = fmin(hi, (i + 1) * dx) - fmax(lo, i * dx);
-        if (ov <= 0.0) continue;
-        const long long c = cell_off[b] + i;
-        const double f = mode == 0 ? field[c] : (sigs[c] - ss_star) - (sigt[c] - st_star);
-        acc += ov * f;
+        const float l = left0 + (float)(i - i0) * dxf;
+        const float ov = fminf(hf, l + dxf) - fmaxf(0.f, l);
+        if (ov <= 0.f) continue;
+        const long long c = c0 + i;
+        if (out0) a0 = fmaf(ov, (float)field[c], a0);
+        if (out1) a1 = fmaf(ov, ((float)sigs[c] - sss) - ((float)sigt[c] - sts), a1);
     }
-    out[e] = (float)(acc / h);
+    const float ih = 1.0f / hf;
+    if (out0) out0[e] = a0 * ih;
+    if (out1) out1[e] = a1 * ih;
 }
 
 // recast source of bin m: PS + PD u_m (+ PL u_{m-1} + PU u_{m+1} with the
@@ -460,7 +471,7 @@ int deeponet_project(nop_ctx* ctx, const double* field_host, float* out_host) {
                                       cudaMemcpyHostToDevice, ctx->stream));
     const long long BM_ = (long long)B * M;
     project_kernel<<<(int)((BM_ + 255) / 256), 256, 0, ctx->stream>>>(
-        B, M, s.cell_off_d, s.ncell_d, s.width_d, f, nullptr, nullptr, 0.0, 0.0, 0, o);
+        B, M, s.cell_off_d, s.ncell_d, s.width_d, f, nullptr, nullptr, 0.0, 0.0, o, nullptr);
     NOP_CUDA_TRY(ctx, cudaGetLastError());
     ctx->count_launch(false);
     NOP_CUDA_TRY(ctx, cudaMemcpyAsync(out_host, o, sizeof(float) * BM_, cudaMemcpyDeviceToHost,
@@ -516,22 +527,17 @@ int deeponet_recast(nop_ctx* ctx, double tol, int itmax, double* phi_d, int* sta
 
     const int mk = ctx->phase_begin(1);
     const long long BM_ = (long long)B * M;
+    // the source on the bins, and (transport) the mismatch from the same pass
     project_kernel<<<(int)((BM_ + 255) / 256), 256, 0, ctx->stream>>>(
         B, M, s.cell_off_d, s.ncell_d, s.width_d, predict_only ? src_d : ctx->src_d,
-        ctx->sigt_d, ctx->sigs_d, c.sigma_t_star, c.sigma_s_star, 0, PS);
-    NOP_CUDA_TRY(ctx, cudaGetLastError());
+        ctx->sigt_d, ctx->sigs_d, c.sigma_t_star, c.sigma_s_star, PS,
+        ctx->diffusion ? nullptr : PD);
     NOP_CUDA_TRY(ctx, cudaGetLastError());
     ctx->count_launch(false);
     if (ctx->diffusion) {
         // Table 1: -dL of -(D u')' + Sigma_a u on the bins; the operator's p*
         // is (D*, Sigma_a*) = (sigma_t_star, sigma_s_star) of its configuration
         NOP_TRY(diffusion_bands(ctx, M, c.sigma_t_star, c.sigma_s_star, PL, PD, PU));
-    } else {
-        project_kernel<<<(int)((BM_ + 255) / 256), 256, 0, ctx->stream>>>(
-            B, M, s.cell_off_d, s.ncell_d, s.width_d, nullptr, ctx->sigt_d, ctx->sigs_d,
-            c.sigma_t_star, c.sigma_s_star, 1, PD);
-        NOP_CUDA_TRY(ctx, cudaGetLastError());
-        ctx->count_launch(false);
     }
     if (predict_only) {
         NOP_CUDA_TRY(ctx, cudaMemsetAsync(PD, 0, sizeof(float) * BM_, ctx->stream));
