@@ -751,13 +751,18 @@ __device__ __forceinline__ void direct_stage(const DirectSmem<T>& sm, int buf, i
 // of psi is the same Fast2Sum as CSum, on pairs.
 __device__ __forceinline__ float2 f2(float x) { return make_float2(x, x); }
 
-__device__ __forceinline__ float2 rcp2(float2 d) {
-    float2 r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(d.x));
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(d.y));
-    const float2 e = __ffma2_rn(make_float2(-d.x, -d.y), r, f2(1.0f));
-    return __ffma2_rn(r, e, r);
+// The direct lanes take the hardware reciprocal as it is (rcp.approx.ftz:
+// within 1 ulp), one rounding more in the update's factor r and no Newton
+// step; the reciprocal of a cell and angle is the same in every iteration,
+// so its error moves the fixed point by rounding size and adds no
+// iteration-to-iteration noise to the stopping test.
+__device__ __forceinline__ float rcp_fast(float d) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+    return r;
 }
+
+__device__ __forceinline__ float2 rcp2(float2 d) { return make_float2(rcp_fast(d.x), rcp_fast(d.y)); }
 
 // P packed pairs of chains over the nk staged steps of `cur` (COMPOSE: chunk
 // maps; otherwise flux partial sums into myred[k]).  r0 holds the reciprocals
@@ -813,7 +818,7 @@ __device__ __forceinline__ void direct_steps_f32(const Cell2<float>* cur, int nk
     for (int k = 0; k < nk; ++k) {
         const float r = r0;
         const Cell2<float> v2 = cur[k + 2];
-        r0 = rcp_dd(fmaf(-0.5f, v1.s0, c));
+        r0 = rcp_fast(fmaf(-0.5f, v1.s0, c));
         const float x = fmaf(S0, h, S1);
         const float d = r * x;
         if constexpr (COMPOSE) {
@@ -877,7 +882,7 @@ __device__ __forceinline__ void direct_pass(const DirectSmem<T>& sm, Cell4<T>* X
         // steps (operands, reciprocals, angle sums) interleaves with the
         // flux chain
         if constexpr (sizeof(T) == 4 && A == 1) {
-            float rr = rcp_dd(fmaf(-0.5f, cur[0].s0, cc[0]));
+            float rr = rcp_fast(fmaf(-0.5f, cur[0].s0, cc[0]));
             direct_steps_f32<COMPOSE>((const Cell2<float>*)cur, nk, (float*)myred, cc[0], wt[0],
                                       psi[0].hi, psi[0].lo, D[0], rr);
         } else if constexpr (sizeof(T) == 4) {
