@@ -774,7 +774,7 @@ __device__ __forceinline__ void direct_steps_f32x2(const Cell2<float>* cur, int 
                                                    float2 (&D2)[P], float2 (&r0)[P]) {
     Cell2<float> v1 = cur[1];
     float S0 = cur[0].s0, S1 = cur[0].s1;
-#pragma unroll 2
+#pragma unroll 4
     for (int k = 0; k < nk; ++k) {
         float2 r[P];
 #pragma unroll
@@ -814,7 +814,7 @@ __device__ __forceinline__ void direct_steps_f32(const Cell2<float>* cur, int nk
                                                  float& r0) {
     Cell2<float> v1 = cur[1];
     float S0 = cur[0].s0, S1 = cur[0].s1;
-#pragma unroll 2
+#pragma unroll 4
     for (int k = 0; k < nk; ++k) {
         const float r = r0;
         const Cell2<float> v2 = cur[k + 2];
@@ -878,9 +878,9 @@ __device__ __forceinline__ void direct_pass(const DirectSmem<T>& sm, Cell4<T>* X
         const Cell2<T>* cur = row + (kb & 1) * (DR + 2);
         // two-deep pipeline: step k loads the operands of step k + 2 and
         // forms the reciprocals of step k + 1 (slots DR, DR + 1 are padding);
-        // two steps per loop trip, so the independent work of consecutive
-        // steps (operands, reciprocals, angle sums) interleaves with the
-        // flux chain
+        // four steps per loop trip in FP32 (two in FP64), so the independent
+        // work of consecutive steps (operands, reciprocals, angle sums)
+        // interleaves with the flux chain
         if constexpr (sizeof(T) == 4 && A == 1) {
             float rr = rcp_fast(fmaf(-0.5f, cur[0].s0, cc[0]));
             direct_steps_f32<COMPOSE>((const Cell2<float>*)cur, nk, (float*)myred, cc[0], wt[0],
