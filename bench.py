@@ -37,7 +37,7 @@ RECAST_ITMAX = 10
 # DRAM bytes (read + write) of one warm-step sweep launch on this workload,
 # from the ncu capture summarised in profiles/sn1d_kernel_4096slab.txt; None
 # once the sweep kernel changes until it is captured again.
-SWEEP_TRAFFIC_BYTES = 70_144_768 + 30_315_264
+SWEEP_TRAFFIC_BYTES = 70_240_000 + 31_363_584
 WORKLOAD = ("4096 slabs, cells U{64..2048}, GL S_N N even U{8..64}, sinusoidal or "
             "piecewise coefficients, Fourier sources, vacuum, tol 1e-6 rel. L2 flux change")
 
