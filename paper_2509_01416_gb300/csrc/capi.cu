@@ -197,22 +197,27 @@ __global__ void rho_kernel(int G, long long C, const long long* cell_off, const 
 // row's excess over its off-diagonal sum: absorption and face leakage), and
 // the iterate of the fundamental mode is positive, so FP32 loses nothing to
 // cancellation.  One warp per instance and group, lane l owning a chunk of
-// ceil(I / 32) cells: each recurrence (the pivots, a Moebius map of
-// t_{k-1} / p_{k-1}; forward substitution; back substitution, affine maps) is
-// composed per chunk, the chunk maps are scanned across the lanes with
-// shuffles, and every lane then runs its chunk from its entry value.  `work`
-// holds six floats per cell and group.  On the 4096-slab batch this predicts
+// ceil(I / 32) cells (rounded up to odd): each recurrence (the pivots, a
+// Moebius map of t_{k-1} / p_{k-1}; forward substitution; back substitution,
+// affine maps) is composed per chunk, the chunk maps are scanned across the
+// lanes with shuffles, and every lane then runs its chunk from its entry
+// value; four inverse iterations.  The six float arrays of an instance sit in
+// shared memory, or for very long instances in `work` (six floats per cell
+// and group).  On the 4096-slab batch this predicts
 // the iteration counts of plain source iteration to 4.6% rms (times a fitted
 // 0.94), where the mean scattering ratio times a leakage factor was off by
 // 26% rms.
-__global__ void __launch_bounds__(128) rho_si_kernel(int B, int G, long long C,
-                                                     const long long* cell_off, const int* ncell,
-                                                     const double* width, const double* sigt,
-                                                     const double* sigs, int refl0, int reflL,
-                                                     float* work, double* rho) {
+// SMEM: one warp per block with the instance's arrays in shared memory
+// (filled by coalesced loads; odd chunks, so the lanes' strided accesses hit
+// 32 different banks); otherwise four warps per block on the global `work`.
+template <bool SMEM>
+__global__ void __launch_bounds__(SMEM ? 32 : 128) rho_si_kernel(
+    int B, int G, long long C, const long long* cell_off, const int* ncell, const double* width,
+    const double* sigt, const double* sigs, int refl0, int reflL, float* work, double* rho) {
     const unsigned FULL = 0xffffffffu;
+    extern __shared__ float rs_sm[];
     const int lane = threadIdx.x & 31;
-    const int e = blockIdx.x * 4 + (threadIdx.x >> 5);
+    const int e = SMEM ? (int)blockIdx.x : (int)blockIdx.x * 4 + (int)(threadIdx.x >> 5);
     if (e >= B * G) return;   // uniform over the warp
     const int b = e / G, g = e % G;
     const int I = ncell[b];
@@ -220,13 +225,22 @@ __global__ void __launch_bounds__(128) rho_si_kernel(int B, int G, long long C,
     const double h = width[b] / I;
     const double* st = sigt + (long long)g * C + o;
     const double* ss = sigs + ((long long)g * G + g) * C + o;
-    float* ipv = work + 6 * ((long long)g * C + o);   // 1 / p_k
+    float* ipv = SMEM ? rs_sm : work + 6 * ((long long)g * C + o);   // 1 / p_k
     float* alf = ipv + I;                            // |l_k| / p_k
     float* cup = alf + I;                            // |u_k| / p_k
     float* ssf = cup + I;                            // Sigma_s
     float* v = ssf + I;                              // iterate
     float* z = v + I;                                // forward-substitution values
-    const int m = (I + 31) / 32;
+    // (SMEM: z first holds sigma_t, read by the pivot passes only)
+    if constexpr (SMEM) {
+        for (int i = lane; i < I; i += 32) {
+            z[i] = (float)st[i];
+            ssf[i] = (float)ss[i];
+        }
+        __syncwarp();
+    }
+    auto stv = [&](int k) { return SMEM ? z[k] : (float)st[k]; };
+    const int m = ((I + 31) / 32) | 1;
     const int k0 = min(I, lane * m), k1 = min(I, k0 + m);
     // face coupling between cells i and i + 1 per unit volume, D_face / h^2
     // with the harmonic D_face = 2 / (3 (sigma_t,i + sigma_t,i+1)); a vacuum
@@ -237,10 +251,10 @@ __global__ void __launch_bounds__(128) rho_si_kernel(int B, int G, long long C,
         return (float)(2.0 * D / ((h + 4.0 * D) * h));
     };
     auto coef = [&](int k, float& lo, float& up, float& a, float& ssk) {
-        const float stk = (float)st[k];
-        ssk = (float)ss[k];
-        lo = k > 0 ? kf / ((float)st[k - 1] + stk) : 0.0f;
-        up = k < I - 1 ? kf / (stk + (float)st[k + 1]) : 0.0f;
+        const float stk = stv(k);
+        ssk = SMEM ? ssf[k] : (float)ss[k];
+        lo = k > 0 ? kf / (stv(k - 1) + stk) : 0.0f;
+        up = k < I - 1 ? kf / (stk + stv(k + 1)) : 0.0f;
         a = fmaxf(stk - ssk, 0.0f);
         if (k == 0 && !refl0) a += leak(st[0]);
         if (k == I - 1 && !reflL) a += leak(st[I - 1]);
@@ -298,10 +312,12 @@ __global__ void __launch_bounds__(128) rho_si_kernel(int B, int G, long long C,
             x = t * ip;
         }
     }
+    // (SMEM: every lane's last read of sigma_t in z precedes the first write of z)
+    __syncwarp();
     // ---- inverse iteration y = A^{-1} Sigma_s v and the Rayleigh quotient
     double mu = 0.0;
     float sc = 1.0f;
-    for (int it = 0; it < 5; ++it) {
+    for (int it = 0; it < 4; ++it) {
         // forward substitution z_k = alf_k z_{k-1} + Sigma_s v_k / p_k
         float A = 1.0f, Bv = 0.0f;
         for (int k = k0; k < k1; ++k) {
@@ -669,12 +685,28 @@ int nop_set_problem(nop_ctx* ctx, const nop_problem* p) {
                                           cudaMemcpyDeviceToHost, ctx->stream));
         NOP_CUDA_TRY(ctx, cudaMemcpyAsync(s.siga_mean.data(), rho_d + B, sizeof(double) * B,
                                           cudaMemcpyDeviceToHost, ctx->stream));
+        // instances of up to about 8000 cells keep their arrays in shared
+        // memory (a block each); longer batches run on a global work array
+        int max_cells = 0;
+        for (int b = 0; b < B; ++b) max_cells = std::max(max_cells, p->n_cells[b]);
+        const size_t rs_smem = sizeof(float) * 6 * (size_t)max_cells;
+        const bool rs_in_smem = rs_smem <= 192 * 1024;
         NOP_TRY(ctx->scratch("rho_si", sizeof(double) * (size_t)B * G +
-                                           sizeof(float) * 6 * (size_t)G * C, &d));
+                                           (rs_in_smem ? 0 : sizeof(float) * 6 * (size_t)G * C),
+                             &d));
         double* rsi_d = (double*)d;
-        rho_si_kernel<<<(B * G + 3) / 4, 128, 0, ctx->stream>>>(
-            B, G, C, s.cell_off_d, s.ncell_d, s.width_d, ctx->sigt_d, ctx->sigs_d, ctx->bc[0],
-            ctx->bc[1], (float*)(rsi_d + (size_t)B * G), rsi_d);
+        if (rs_in_smem) {
+            NOP_CUDA_TRY(ctx, cudaFuncSetAttribute(rho_si_kernel<true>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)rs_smem));
+            rho_si_kernel<true><<<B * G, 32, rs_smem, ctx->stream>>>(
+                B, G, C, s.cell_off_d, s.ncell_d, s.width_d, ctx->sigt_d, ctx->sigs_d, ctx->bc[0],
+                ctx->bc[1], nullptr, rsi_d);
+        } else {
+            rho_si_kernel<false><<<(B * G + 3) / 4, 128, 0, ctx->stream>>>(
+                B, G, C, s.cell_off_d, s.ncell_d, s.width_d, ctx->sigt_d, ctx->sigs_d, ctx->bc[0],
+                ctx->bc[1], (float*)(rsi_d + (size_t)B * G), rsi_d);
+        }
         NOP_CUDA_TRY(ctx, cudaGetLastError());
         std::vector<double> rsi((size_t)B * G);
         NOP_CUDA_TRY(ctx, cudaMemcpyAsync(rsi.data(), rsi_d, sizeof(double) * B * G,
