@@ -1972,15 +1972,16 @@ int sn1d_run(nop_ctx* ctx, const nop_solve_opts* o, bool eigen, const double* ph
         // latencies + 12 x team latencies) / warps gets a team (a team costs
         // more SM time than one warp, so only the instances that would outlast
         // the batch are worth it).  The margin covers the error of the latency
-        // estimates: 1.25 when the iteration counts are estimated (about 15%
-        // rms behind a warm start), 1.05 when they are those of the previous
-        // solve of the layout.
+        // estimates: 1.1 when the iteration counts are estimated, 1.05 when
+        // they are those of the previous solve of the layout (on the
+        // 4096-slab batch a margin of 1.0 left a straggler, 1.05-1.1 gave the
+        // shortest step, and every 0.15 above that added teams and about 3%).
         std::vector<char> team;
         double span = 0.0;
         const bool known_its = !cold && !eigen && (int)last.size() == B;
         NOP_TRY(sn1d_select_teams(B, lw.data(), lt.data(), warps_total, NW,
                                   o->schedule == NOP_SCHED_BLOCK ? 1 : (o->schedule == NOP_SCHED_WARP || B < 2 ? 2 : 0),
-                                  known_its ? 1.05 : 1.25, team, &span));
+                                  known_its ? 1.05 : 1.1, team, &span));
         cfg.assign(B, 0);
         std::vector<double> cost(B);
         double big_work = 0, small_work = 0;
