@@ -59,6 +59,8 @@ struct SlabDev {
     std::vector<double> siga_mean;   // host: mean absorption of the group that sets rho
     std::vector<double> rho_si;      // host: diffusion estimate of the source iteration's
                                      // spectral radius (largest over groups)
+    std::vector<int> gl_orders, gl_offs;   // host: the orders whose Gauss-Legendre sets
+                                           // are built, and where each set starts
     std::vector<int> last_iters;     // host: iterations of each instance in the last solve
     // the last slab schedule and the hash of what it was computed from
     std::vector<int> plan_small, plan_big, plan_cfg;

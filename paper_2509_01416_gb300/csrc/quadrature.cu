@@ -86,16 +86,23 @@ int build_gauss_legendre(nop_ctx* ctx) {
     s.w_d = (double*)p;
     NOP_TRY(ctx->scratch("gl_qoff", s.n_inst * sizeof(int), &p));
     s.qoff_d = (int*)p;
-    NOP_CUDA_TRY(ctx, cudaMemcpyAsync(ords_d, ords.data(), ords.size() * sizeof(int),
-                                      cudaMemcpyHostToDevice, ctx->stream));
-    NOP_CUDA_TRY(ctx, cudaMemcpyAsync(offs_d, offs.data(), offs.size() * sizeof(int),
-                                      cudaMemcpyHostToDevice, ctx->stream));
     NOP_CUDA_TRY(ctx, cudaMemcpyAsync(s.qoff_d, s.qoff_h.data(), s.n_inst * sizeof(int),
                                       cudaMemcpyHostToDevice, ctx->stream));
-    gauss_legendre_kernel<<<(int)ords.size(), 64, 0, ctx->stream>>>(ords_d, offs_d,
-                                                                   (int)ords.size(), s.mu_d,
-                                                                   s.w_d);
-    NOP_CUDA_TRY(ctx, cudaGetLastError());
+    // the sets depend on the orders and their offsets (the order in which the
+    // orders first appear in the batch): a new problem with both unchanged
+    // keeps the sets already built
+    if (ords != s.gl_orders || offs != s.gl_offs) {
+        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(ords_d, ords.data(), ords.size() * sizeof(int),
+                                          cudaMemcpyHostToDevice, ctx->stream));
+        NOP_CUDA_TRY(ctx, cudaMemcpyAsync(offs_d, offs.data(), offs.size() * sizeof(int),
+                                          cudaMemcpyHostToDevice, ctx->stream));
+        gauss_legendre_kernel<<<(int)ords.size(), 64, 0, ctx->stream>>>(ords_d, offs_d,
+                                                                       (int)ords.size(), s.mu_d,
+                                                                       s.w_d);
+        NOP_CUDA_TRY(ctx, cudaGetLastError());
+        s.gl_orders = ords;
+        s.gl_offs = offs;
+    }
     // host copies of the orders must stay valid until the copies above complete
     NOP_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
     return NOP_OK;
